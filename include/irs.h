@@ -1,0 +1,188 @@
+/*
+ * irs.h -- C ABI of the GB300 inverse ray-shooting library.
+ *
+ * The library computes gravitational-microlensing magnification maps by
+ * inverse ray-shooting (IRS) as described in Zheng, Chen, Li & Chen,
+ * "An Improved GPU-Based Ray-Shooting Code For Gravitational Microlensing"
+ * (arXiv:2204.10871): a regular lattice of rays over a rectangular
+ * image/lens plane is deflected by point lenses, a smooth convergence
+ * kappa_s, an external shear gamma and a negative mass sheet, and the rays
+ * landing in each source-plane pixel are counted.
+ *
+ * Conventions for every entry point:
+ *  - All lengths are in Einstein radii of a unit-mass lens.
+ *  - Lens positions are interleaved doubles (x0, y0, x1, y1, ...), masses are
+ *    doubles; both live in DEVICE memory owned by the caller.
+ *  - Maps are row-major [npix_y][npix_x]; counts are uint32, magnifications
+ *    float; both in DEVICE memory owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls enqueue work and return without waiting for it, except
+ *    where noted.  Errors detected on the host are returned at once; errors
+ *    raised by kernels are kept in the plan and returned by irs_plan_sync.
+ *  - The library never aborts, throws or prints.  A plan is not thread-safe:
+ *    use one plan per host thread or serialise calls on it.
+ */
+#ifndef IRS_GB300_H
+#define IRS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum irs_status {
+  IRS_OK = 0,
+  IRS_ERR_ARG = 1,          /* invalid argument (NULL pointer, bad size, NaN) */
+  IRS_ERR_DEGENERATE = 2,   /* |1 - kappa -+ gamma| < 1e-6: the mean lens map is singular */
+  IRS_ERR_OOM = 3,          /* device allocation failed */
+  IRS_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  IRS_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  IRS_ERR_OVERFLOW = 6,     /* a size exceeds what the kernels index */
+  IRS_ERR_NOT_TRAINED = 7,  /* IRS_MLP requested before the far-field network was trained */
+  IRS_ERR_UNSUPPORTED = 8   /* combination of options not implemented */
+} irs_status;
+
+/* Shape of the lens plane.  RECT: the image rectangle is the lens plane and the
+ * negative sheet is the rectangle's closed form (Eq. alpha1 and Appendix A).
+ * CIRCLE: lenses fill the circumscribed circle and the sheet is the circular
+ * -kappa_* theta of Eq. (alphapart), i.e. the deflection of Eq. (alpha). */
+typedef enum irs_plane { IRS_PLANE_RECT = 0, IRS_PLANE_CIRCLE = 1 } irs_plane;
+
+/* How the lens sum is evaluated.  BRUTE: every ray sums every lens.  INTERP:
+ * lenses in the ray's level-1 cell and its 8 neighbours are summed per ray,
+ * the rest come from a per-cell Taylor series of the far field (Sec. 2.4,
+ * "Interpolation algorithm").  MLP: as INTERP with part of the far field
+ * taken from a trained coordinate network (falls back to INTERP if untrained). */
+typedef enum irs_method { IRS_BRUTE = 0, IRS_INTERP = 1, IRS_MLP = 2 } irs_method;
+
+/* Inputs of the flow chart ("Input parameters", Sec. 2.4). */
+typedef struct irs_params {
+  double kappa_star;      /* convergence in point lenses, kappa_* (sizes the plane) */
+  double kappa_s;         /* smooth convergence kappa_s */
+  double gamma;           /* external shear */
+  double src_x0, src_x1;  /* source region [x0, x1) x [y0, y1) */
+  double src_y0, src_y1;
+  int32_t npix_x, npix_y; /* source-plane pixels */
+  double rays_per_pixel;  /* rays per source pixel in the unlensed map (N_av) */
+  double border;          /* protective border P; < 0 selects the paper's 10 sqrt(kappa_*) */
+  int64_t n_star;         /* lens count the cell grid and workspace are sized for; 0 = kappa_* A / pi */
+  int32_t plane;          /* irs_plane */
+  int32_t method;         /* irs_method */
+  uint32_t flags;         /* reserved, must be 0 */
+  int32_t far_order;      /* INTERP: terms of the per-cell far-field series; 0 = default */
+  double cell_mult;       /* INTERP: level-1 cell side in units of the paper's rule; 0 = default */
+  int32_t window;         /* INTERP: cells within this Chebyshev distance sum lenses directly into
+                             the series; 0 = default */
+  int32_t reserved[7];    /* must be 0 */
+} irs_params;
+
+/* Geometry chosen by irs_plan (FP64, host side). */
+typedef struct irs_plan_info {
+  double lens_x0, lens_x1, lens_y0, lens_y1; /* image/lens rectangle [a1,a2] x [b1,b2] */
+  double center_x, center_y;                 /* rectangle centre */
+  double border;                             /* P actually used */
+  double dx_ray;                             /* level-3 spacing Delta x3 */
+  double pix_x, pix_y;                       /* source pixel sides */
+  double circle_r;                           /* circumscribed-circle radius */
+  double cell_x, cell_y;                     /* level-1 cell sides (INTERP) */
+  int64_t n_rays_x, n_rays_y, n_rays;        /* ray lattice */
+  int64_t n_star_suggested;                  /* kappa_* A / pi (unit mean mass) */
+  int32_t ncell_x, ncell_y;                  /* level-1 grid (INTERP) */
+  int32_t rays_per_cell_x, rays_per_cell_y;  /* rays along a cell side (INTERP) */
+  int32_t far_order, window;                 /* INTERP series terms and direct window */
+  int64_t workspace_bytes;                   /* device memory held by the plan */
+} irs_plan_info;
+
+typedef struct irs_plan irs_plan_t;
+
+/* Size the image/lens plane and the ray lattice from `params` (flow chart:
+ * protective border P = 10 sqrt(kappa_*), I = (S + 2P)/|1 - kappa -+ gamma|,
+ * level-3 spacing; Sec. 2.4) and allocate the plan's device workspace on the
+ * current device.  Synchronous (it allocates).  On success *out owns the
+ * plan; release it with irs_plan_destroy.  Errors: IRS_ERR_ARG,
+ * IRS_ERR_DEGENERATE, IRS_ERR_OOM, IRS_ERR_OVERFLOW. */
+irs_status irs_plan(const irs_params* params, void* stream, irs_plan_t** out);
+
+/* Copy the plan's geometry into *info (host memory).  Errors: IRS_ERR_ARG. */
+irs_status irs_plan_info_get(const irs_plan_t* plan, irs_plan_info* info);
+
+/* One magnification map (the whole flow chart after sizing, Sec. 2.4):
+ * deflect every ray of the lattice by the n lenses (lens_xy: 2n doubles,
+ * mass: n doubles, device), bin it into the source pixel it lands in, and
+ * write counts (npix_x*npix_y uint32, device, overwritten) and, when `mag` is
+ * not NULL, Mag_ij = N_ij S_I / S_S (npix_x*npix_y float, device).  The
+ * sheet's density is that of the lenses passed in, pi sum(m) / area.  n may
+ * be 0.  Asynchronous on `stream`; may grow the workspace (synchronising) if
+ * n exceeds the size the plan was made for.  Errors: IRS_ERR_ARG,
+ * IRS_ERR_OOM, IRS_ERR_CUDA, IRS_ERR_NOT_TRAINED. */
+irs_status irs_make_map(irs_plan_t* plan, const double* lens_xy, const double* mass, int64_t n,
+                        uint32_t* counts, float* mag, void* stream);
+
+/* Several maps with their own plans, lenses and outputs, enqueued as one
+ * persistent work queue per stage and replayed from a CUDA graph that is
+ * captured on the first call with the same plans and pointers.  Arrays hold
+ * `nmaps` host-side entries; the pointers they hold are device pointers.
+ * Errors as irs_make_map, plus IRS_ERR_TIMEOUT from the queue's bounded wait. */
+irs_status irs_make_maps_batched(irs_plan_t* const* plans, int32_t nmaps,
+                                 const double* const* lens_xy, const double* const* mass,
+                                 const int64_t* n, uint32_t* const* counts, float* const* mag,
+                                 void* stream);
+
+/* Chunked sweep (the count map is additive over disjoint sets of rays): add
+ * into `counts` (device, NOT cleared) the rays of lattice rows
+ * [row0, row1) only.  Used to sweep very large lattices in pieces and to
+ * resume a sweep from a saved map plus the next row.  The sheet density and
+ * all per-map constants are recomputed from the lenses on every call.
+ * Errors: IRS_ERR_ARG (row range outside [0, n_rays_y]), as irs_make_map. */
+irs_status irs_make_map_rows(irs_plan_t* plan, const double* lens_xy, const double* mass,
+                             int64_t n, int64_t row0, int64_t row1, uint32_t* counts,
+                             void* stream);
+
+/* Mag_ij = N_ij S_I / S_S of an existing count map (device in, device out). */
+irs_status irs_magnify(irs_plan_t* plan, const uint32_t* counts, float* mag, void* stream);
+
+/* Stage times of the last map made with this plan, from CUDA events recorded
+ * on the launching stream (enable with irs_plan_set_timing; synchronises on
+ * the events when read).  Fields are milliseconds; ms_raypass is the ray pass
+ * kernel alone, the dominant kernel of every method. */
+typedef struct irs_timings {
+  float ms_total;     /* first to last event of the map */
+  float ms_prep;      /* mass sum and per-tile / per-cell setup */
+  float ms_cells;     /* INTERP: lens cell lists */
+  float ms_farfield;  /* INTERP: far-field series */
+  float ms_raypass;   /* ray pass incl. binning */
+  float ms_magnify;   /* magnification (0 if not requested) */
+  int64_t rays;       /* rays shot by the timed map */
+  int32_t valid;      /* 1 when the fields hold a measurement */
+  int32_t pad_;
+} irs_timings;
+
+irs_status irs_plan_set_timing(irs_plan_t* plan, int32_t enable);
+irs_status irs_plan_timings(irs_plan_t* plan, irs_timings* out);
+
+/* Debug / parity path: the source-plane position beta (2 doubles per ray,
+ * device) and pixel index (int64, -1 when outside; device; may be NULL) of
+ * the lattice rays with flat indices ray_idx[k] = j * n_rays_x + i (device
+ * int64).  Each ray is computed by the same kernel code and tiling that
+ * irs_make_map uses for the plan's method, so the values are those that
+ * were binned.  Errors: IRS_ERR_ARG, IRS_ERR_CUDA. */
+irs_status irs_shoot_rays(irs_plan_t* plan, const double* lens_xy, const double* mass, int64_t n,
+                          const int64_t* ray_idx, int64_t n_idx, double* beta, int64_t* pixel,
+                          void* stream);
+
+/* Wait for `stream` and return the first error a kernel of this plan raised
+ * since the last sync (IRS_OK if none), clearing it. */
+irs_status irs_plan_sync(irs_plan_t* plan, void* stream);
+
+/* Free the plan and its workspace (synchronises the device).  NULL is a no-op. */
+irs_status irs_plan_destroy(irs_plan_t* plan);
+
+/* Static text for a status code. */
+const char* irs_status_str(irs_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IRS_GB300_H */

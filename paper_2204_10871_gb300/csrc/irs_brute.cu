@@ -1,0 +1,340 @@
+// irs_brute.cu -- plain ("ordinary GPU IRS") ray pass: every ray sums every
+// lens (arXiv:2204.10871, Sec. 1 and the "ordinary GPU-based IRS code" of
+// Sec. 3.1), with the rectangular negative sheet of Eq. (alpha1) / Appendix A.
+//
+// Layout of the work: the ray lattice is cut into tiles of 32 x 64 rays.  A
+// CTA of 8 warps owns one tile at a time (persistent grid); lane l takes
+// column i0 + l and each warp 8 consecutive rows, so a thread carries 8 rays
+// that share their x offset.  Lenses stream through shared memory 256 at a
+// time as FP32 positions relative to the tile centre (converted from the
+// caller's FP64 once per tile and stage) and are broadcast to all warps.
+//
+// Precision plan: per pair FP32 with rcp.approx on the SFU; each 256-lens
+// stage is summed in FP32 and folded into a TwoSum (hi, lo) accumulator; the
+// sheet, the smooth terms and the pixel base of the tile centre are FP64 in
+// the setup kernel and reach the rays as double-float constants plus an
+// FP32 Taylor series of the sheet's analytic part in the ray's offset t.
+#include <math.h>
+
+#include "irs_common.cuh"
+
+namespace irs {
+
+// ------------------------------------------------------------ mass sum (FP64)
+// Deterministic two-pass sum of the masses: fixed strides per thread, fixed
+// reduction tree, fixed order of the block partials.
+__global__ void k_mass_partial(const double* __restrict__ mass, int64_t n,
+                               double* __restrict__ part) {
+  __shared__ double sh[MSUM_THREADS];
+  double s = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) s += mass[k];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = MSUM_THREADS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_mass_final(const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < MSUM_BLOCKS; ++b) s += part[b];
+    out[0] = s;
+  }
+}
+
+cudaError_t launch_mass_sum(const irs_plan_t* P, const double* mass, int64_t n, cudaStream_t s) {
+  k_mass_partial<<<MSUM_BLOCKS, MSUM_THREADS, 0, s>>>(mass, n, P->d_mpart);
+  k_mass_final<<<1, 32, 0, s>>>(P->d_mpart, P->d_msum);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ FP64 complex
+struct cd {
+  double re, im;
+};
+__device__ __forceinline__ cd cmul(cd a, cd b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__device__ __forceinline__ cd crecip(cd a) {
+  const double d = a.re * a.re + a.im * a.im;
+  return {a.re / d, -a.im / d};
+}
+// principal Log
+__device__ __forceinline__ cd clog_p(cd a) {
+  return {0.5 * log(a.re * a.re + a.im * a.im), atan2(a.im, a.re)};
+}
+
+// ------------------------------------------------------------ tile setup
+// Analytic part of the positive rectangle sheet (complex form derived from the
+// appendix integrals): inside the rectangle,
+//   conj(alpha_sheet)(z) = kappa_* conj(z) + g(z),
+//   g(z) = kappa_* (z - 2 a2) + sum_c phi_c(z),
+//   phi_c(z) = -i a_c (z - c) Log(z - c),   a_c = (kappa_*/pi) s_c,
+// with corner signs s = +1 at (a1,b1) and (a2,b2), -1 at (a2,b1) and (a1,b2).
+// Derivatives: phi_c' = -i a_c (Log(z-c) + 1),
+//              phi_c^(n) = -i a_c (-1)^n (n-2)! / (z-c)^(n-1)  (n >= 2).
+// Corners closer than 6 tile half-diagonals are left out of the series and
+// evaluated per ray instead (the series would converge slowly there).
+__global__ void k_brute_setup(Geo g, const double* __restrict__ msum, int64_t ntx, int64_t ntiles,
+                              TileRec* __restrict__ recs) {
+  const int64_t tile = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tile >= ntiles) return;
+  const TileGeo tg = tile_geo(g, tile, ntx);
+  const double ks = g.kstar_scale * msum[0];  // kappa_*^act (reading R2)
+  const double kap = g.kappa_s + ks;
+  const double zx = g.a1 + tg.ci * g.dx3, zy = g.b1 + tg.cj * g.dx3;
+
+  // base pixel from the mean lens map of the tile centre
+  const double m1 = (1.0 - kap - g.gamma) * zx, m2 = (1.0 - kap + g.gamma) * zy;
+  double fx = floor((m1 - g.src_x0) / g.sx), fy = floor((m2 - g.src_y0) / g.sy);
+  fx = fmin(fmax(fx, -1.0e9), 1.0e9);
+  fy = fmin(fmax(fy, -1.0e9), 1.0e9);
+  const double base_x = g.src_x0 + fx * g.sx, base_y = g.src_y0 + fy * g.sy;
+
+  TileRec r;
+  r.ix = (int32_t)fx;
+  r.iy = (int32_t)fy;
+  r.n_near = 0;
+  r.pad_ = 0;
+  for (int k = 0; k < SHEET_TERMS; ++k) r.T[k][0] = r.T[k][1] = 0.f;
+  for (int k = 0; k < MAX_NEAR; ++k) r.near[k][0] = r.near[k][1] = r.near[k][2] = r.near[k][3] = 0.f;
+
+  double cre, cim;  // conj(beta) of the centre without the lens sum
+  if (g.plane == IRS_PLANE_CIRCLE) {
+    // Eq. (alpha) + k_* theta_c:  conj(beta) = (1-k_s) conj(z) - g z - k_* conj(z_c) - L
+    cre = (1.0 - g.kappa_s - g.gamma) * zx - ks * g.cx;
+    cim = -(1.0 - g.kappa_s + g.gamma) * zy + ks * g.cy;
+  } else {
+    // Eq. (alpha1): conj(beta) = (1-k) conj(z) - g z - L + conj(alpha_sheet,+)
+    cd T0 = {ks * (2.0 * zx - 2.0 * g.a2), 0.0};  // kappa_* (conj z + z - 2 a2)
+    cd T[SHEET_TERMS];
+    for (int k = 0; k < SHEET_TERMS; ++k) T[k] = {0.0, 0.0};
+    T[0].re = ks;  // derivative of kappa_* (z - 2 a2)
+    const double half_diag = 0.5 * g.dx3 * hypot((double)(tg.i1 - tg.i0), (double)(tg.j1 - tg.j0));
+    const double rho = 6.0 * fmax(half_diag, g.dx3);
+    const double cxs[4] = {g.a1, g.a2, g.a1, g.a2};
+    const double cys[4] = {g.b1, g.b1, g.b2, g.b2};
+    const double sgn[4] = {1.0, -1.0, -1.0, 1.0};
+    for (int c = 0; c < 4; ++c) {
+      const double ac = ks / M_PI * sgn[c];
+      const cd w = {zx - cxs[c], zy - cys[c]};
+      if (ac == 0.0) continue;
+      if (hypot(w.re, w.im) < rho && r.n_near < MAX_NEAR) {
+        r.near[r.n_near][0] = (float)w.re;
+        r.near[r.n_near][1] = (float)w.im;
+        r.near[r.n_near][2] = (float)ac;
+        r.n_near++;
+        continue;
+      }
+      const cd L = clog_p(w);
+      const cd wl = cmul(w, L);
+      T0.re += ac * wl.im;  // -i a_c (w L)
+      T0.im -= ac * wl.re;
+      T[0].re += ac * L.im;  // -i a_c (L + 1)
+      T[0].im -= ac * (L.re + 1.0);
+      const cd inv = crecip(w);
+      cd pw = inv;
+      for (int n = 2; n <= SHEET_TERMS; ++n) {
+        const double coef = ((n & 1) ? -1.0 : 1.0) / (double)(n * (n - 1));
+        T[n - 1].re += ac * coef * pw.im;
+        T[n - 1].im -= ac * coef * pw.re;
+        pw = cmul(pw, inv);
+      }
+    }
+    cre = (1.0 - kap - g.gamma) * zx + T0.re;
+    cim = -(1.0 - kap + g.gamma) * zy + T0.im;
+    for (int k = 0; k < SHEET_TERMS; ++k) {
+      r.T[k][0] = (float)T[k].re;
+      r.T[k][1] = (float)T[k].im;
+    }
+  }
+  split_df(cre - base_x, r.cx_hi, r.cx_lo);
+  split_df(-cim - base_y, r.cy_hi, r.cy_lo);
+  recs[tile] = r;
+}
+
+cudaError_t launch_brute_setup(const irs_plan_t* P, cudaStream_t s) {
+  const int64_t nt = P->br_ntiles;
+  const int threads = 128;
+  const int64_t blocks = (nt + threads - 1) / threads;
+  k_brute_setup<<<(unsigned)blocks, threads, 0, s>>>(P->g, P->d_msum, P->br_ntx, nt, P->d_tiles);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ ray pass
+enum { MODE_MAP = 0, MODE_DUMP = 1 };
+
+template <int MODE>
+__global__ void __launch_bounds__(BR_THREADS, 2)
+k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, int64_t n,
+        const TileRec* __restrict__ recs, int64_t ntx, int64_t nwork, int64_t row0, int64_t row1,
+        uint32_t* __restrict__ counts, const int64_t* __restrict__ idx,
+        double* __restrict__ beta_out, int64_t* __restrict__ pix_out) {
+  __shared__ float4 lens_s[BR_LT];
+  __shared__ TileRec rec;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int64_t work = blockIdx.x; work < nwork; work += gridDim.x) {
+    int64_t tile, want_i = -1, want_j = -1;
+    if (MODE == MODE_MAP) {
+      tile = (row0 / BR_TY) * ntx + work;  // tile rows covering [row0, row1)
+    } else {
+      const int64_t f = idx[work];
+      want_i = f % g.nrx;
+      want_j = f / g.nrx;
+      tile = (want_j / BR_TY) * ntx + want_i / BR_TX;
+    }
+    const TileGeo tg = tile_geo(g, tile, ntx);
+    const double zx = g.a1 + tg.ci * g.dx3, zy = g.b1 + tg.cj * g.dx3;
+    const int64_t col = tg.i0 + lane;
+    const float tx = (float)(((double)col + 0.5 - tg.ci) * g.dx3);
+    float ty[BR_R];
+#pragma unroll
+    for (int r = 0; r < BR_R; ++r)
+      ty[r] = (float)(((double)(tg.j0 + warp * BR_R + r) + 0.5 - tg.cj) * g.dx3);
+
+    float axh[BR_R], axl[BR_R], ayh[BR_R], ayl[BR_R];
+#pragma unroll
+    for (int r = 0; r < BR_R; ++r) axh[r] = axl[r] = ayh[r] = ayl[r] = 0.f;
+
+    __syncthreads();  // previous tile's readers of rec / lens_s are done
+    if (tid == 0) rec = recs[tile];
+
+    for (int64_t base = 0; base < n; base += BR_LT) {
+      const int64_t k = base + tid;
+      float4 v = make_float4(1.0e15f, 1.0e15f, 0.f, 0.f);  // padding: massless, far away
+      if (k < n) {
+        const double2 p = xy[k];
+        v = make_float4((float)(p.x - zx), (float)(p.y - zy), (float)mass[k], 0.f);
+      }
+      __syncthreads();
+      lens_s[tid] = v;
+      __syncthreads();
+      float pax[BR_R], pay[BR_R];
+#pragma unroll
+      for (int r = 0; r < BR_R; ++r) pax[r] = pay[r] = 0.f;
+#pragma unroll 2
+      for (int jl = 0; jl < BR_LT; ++jl) {
+        const float4 L = lens_s[jl];
+        const float dx = tx - L.x;
+        const float dx2 = dx * dx;
+#pragma unroll
+        for (int r = 0; r < BR_R; ++r) {
+          const float dy = ty[r] - L.y;
+          const float r2 = fmaf(dy, dy, dx2);
+          const float w = L.z * rcp_approx(r2);
+          pax[r] = fmaf(w, dx, pax[r]);
+          pay[r] = fmaf(w, dy, pay[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < BR_R; ++r) {
+        float s, e;
+        two_sum(axh[r], pax[r], s, e);
+        axh[r] = s;
+        axl[r] += e;
+        two_sum(ayh[r], pay[r], s, e);
+        ayh[r] = s;
+        ayl[r] += e;
+      }
+    }
+    __syncthreads();  // rec visible
+
+    // ---- per-ray: smooth terms, sheet series, near corners, pixel
+#pragma unroll
+    for (int r = 0; r < BR_R; ++r) {
+      const int64_t row = tg.j0 + warp * BR_R + r;
+      const bool inside = (col < tg.i1) && (row < tg.j1) && (row >= row0) && (row < row1);
+      // P(t) = sum_n T_n t^n by Horner, complex FP32
+      float pr = 0.f, pi = 0.f;
+#pragma unroll
+      for (int k = SHEET_TERMS - 1; k >= 0; --k) {
+        const float ar = rec.T[k][0] + pr, ai = rec.T[k][1] + pi;
+        pr = ar * tx - ai * ty[r];
+        pi = ar * ty[r] + ai * tx;
+      }
+      for (int c = 0; c < rec.n_near; ++c) {
+        const float wr = rec.near[c][0] + tx, wi = rec.near[c][1] + ty[r];
+        const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
+        const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;  // w Log w
+        pr += rec.near[c][2] * pli;                                    // -i a_c (w Log w)
+        pi -= rec.near[c][2] * plr;
+      }
+      float s1, e1, s2, e2;
+      two_sum(rec.cx_hi, -axh[r], s1, e1);
+      two_sum(rec.cy_hi, -ayh[r], s2, e2);
+      const float b1 = s1 + (((e1 + rec.cx_lo) - axl[r]) + (g.lam_s1 * tx + pr));
+      const float b2 = s2 + (((e2 + rec.cy_lo) - ayl[r]) + (g.lam_s2 * ty[r] - pi));
+      uint32_t key = 0;
+      int64_t pix = -1;
+      const bool ok = inside && pixel_from_rel(g, rec.ix, rec.iy, b1, b2, key, pix);
+      if (MODE == MODE_MAP) {
+        bin_warp(counts, ok, key);
+      } else {
+        if (col == want_i && row == want_j) {
+          beta_out[2 * work] = (g.src_x0 + (double)rec.ix * g.sx) + (double)b1;
+          beta_out[2 * work + 1] = (g.src_y0 + (double)rec.iy * g.sy) + (double)b2;
+          if (pix_out) pix_out[work] = pix;
+        }
+      }
+    }
+  }
+}
+
+int brute_grid_size(int num_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_brute<MODE_MAP>, BR_THREADS, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return num_sms * per_sm;
+}
+
+cudaError_t launch_brute_map(const irs_plan_t* P, const double* xy, const double* mass, int64_t n,
+                             int64_t row0, int64_t row1, uint32_t* counts, cudaStream_t s) {
+  if (row1 <= row0) return cudaSuccess;
+  const int64_t tr0 = row0 / BR_TY, tr1 = (row1 + BR_TY - 1) / BR_TY;
+  const int64_t nwork = (tr1 - tr0) * P->br_ntx;
+  const int64_t grid = nwork < P->br_grid ? nwork : P->br_grid;
+  k_brute<MODE_MAP><<<(unsigned)grid, BR_THREADS, 0, s>>>(
+      P->g, reinterpret_cast<const double2*>(xy), mass, n, P->d_tiles, P->br_ntx, nwork, row0,
+      row1, counts, nullptr, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_brute_dump(const irs_plan_t* P, const double* xy, const double* mass, int64_t n,
+                              const int64_t* idx, int64_t nidx, double* beta, int64_t* pix,
+                              cudaStream_t s) {
+  const int64_t grid = nidx < P->br_grid ? nidx : P->br_grid;
+  k_brute<MODE_DUMP><<<(unsigned)grid, BR_THREADS, 0, s>>>(
+      P->g, reinterpret_cast<const double2*>(xy), mass, n, P->d_tiles, P->br_ntx, nidx, 0,
+      P->g.nry, nullptr, idx, beta, pix);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ magnification
+// Mag_ij = N_ij * S_I / S_S with S_I = dx3^2 and S_S = s_x s_y ("Calculate the
+// magnification of each pixel", Sec. 2.4).
+__global__ void k_magnify(const uint32_t* __restrict__ counts, float* __restrict__ mag, int64_t npix,
+                          float ratio) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npix; k += stride)
+    mag[k] = (float)counts[k] * ratio;
+}
+
+cudaError_t launch_magnify(const irs_plan_t* P, const uint32_t* counts, float* mag, cudaStream_t s) {
+  const int64_t npix = (int64_t)P->g.npix_x * P->g.npix_y;
+  const float ratio = (float)(P->g.dx3 * P->g.dx3 / (P->g.sx * P->g.sy));
+  int64_t blocks = (npix + 255) / 256;
+  const int64_t cap = (int64_t)P->num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_magnify<<<(unsigned)blocks, 256, 0, s>>>(counts, mag, npix, ratio);
+  return cudaGetLastError();
+}
+
+}  // namespace irs

@@ -1,0 +1,165 @@
+// irs_common.cuh -- shared definitions of the CUDA library (not of the oracle).
+//
+// Complex notation used throughout the kernels: z = theta_1 + i theta_2.  A
+// point lens m at z_i deflects by m (theta - theta_i)/|theta - theta_i|^2,
+// which is conj(m / (z - z_i)), so the lens sum of Eq. (alpha1) is
+// conj(L(z)) with L(z) = sum_i m_i / (z - z_i) analytic away from the lenses.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/irs.h"
+
+namespace irs {
+
+// ---------------------------------------------------------------- geometry
+// Everything a kernel needs to know about one plan, passed by value.
+struct Geo {
+  double a1, a2, b1, b2;   // image/lens rectangle
+  double cx, cy;           // rectangle centre (= circle centre)
+  double dx3;              // ray spacing
+  double src_x0, src_y0;   // source region origin
+  double sx, sy;           // source pixel sides
+  double kappa_s, gamma;
+  double kstar_scale;      // kappa_*^act = kstar_scale * sum(m): pi/A (rect) or 1/R^2 (circle)
+  int64_t nrx, nry;        // ray lattice
+  int32_t npix_x, npix_y;
+  int32_t plane;           // irs_plane
+  int32_t pad_;
+  float inv_sx, inv_sy;    // 1 / pixel side (FP32)
+  float lam_s1, lam_s2;    // 1 - kappa_s - gamma, 1 - kappa_s + gamma
+};
+
+// ---------------------------------------------------------------- FP32 helpers
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest, no contraction).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Split an FP64 value into FP32 hi + lo with hi + lo == x to ~2^-48 relative.
+__device__ __host__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// Warp-aggregated increment of counts[key] for every lane with valid == true:
+// lanes that share a pixel elect one leader that adds their number.
+__device__ __forceinline__ void bin_warp(uint32_t* counts, bool valid, uint32_t key) {
+  const uint32_t k = valid ? key : 0xFFFFFFFFu;
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+  const int lane = threadIdx.x & 31;
+  if (valid && lane == __ffs(peers) - 1) atomicAdd(counts + key, (uint32_t)__popc(peers));
+}
+
+// Pixel of a ray from its position relative to the base pixel's lower-left
+// corner (brel1, brel2 in theta_E) -- reading R7, floor per axis.
+__device__ __forceinline__ bool pixel_from_rel(const Geo& g, int32_t ix, int32_t iy, float brel1,
+                                               float brel2, uint32_t& key, int64_t& pix) {
+  pix = -1;
+  if (!(isfinite(brel1) && isfinite(brel2))) return false;
+  const float f1 = floorf(brel1 * g.inv_sx), f2 = floorf(brel2 * g.inv_sy);
+  if (!(fabsf(f1) < 1.0e9f && fabsf(f2) < 1.0e9f)) return false;
+  const int64_t px = (int64_t)ix + (int64_t)f1, py = (int64_t)iy + (int64_t)f2;
+  if (px < 0 || px >= g.npix_x || py < 0 || py >= g.npix_y) return false;
+  pix = py * (int64_t)g.npix_x + px;
+  key = (uint32_t)pix;
+  return true;
+}
+
+// ---------------------------------------------------------------- brute force
+constexpr int BR_TX = 32;             // tile columns: one per lane
+constexpr int BR_WARPS = 8;           // warps per CTA
+constexpr int BR_R = 8;               // rays (rows) per thread
+constexpr int BR_TY = BR_WARPS * BR_R;
+constexpr int BR_THREADS = BR_WARPS * 32;
+constexpr int BR_LT = 256;            // lenses per shared-memory stage (= FP32 partial length)
+constexpr int SHEET_TERMS = 8;        // Taylor terms t^1..t^8 of the sheet's analytic part
+constexpr int MAX_NEAR = 4;           // rectangle corners evaluated per ray
+
+// Per-tile constants computed in FP64 by the setup kernel.
+struct __align__(16) TileRec {
+  float cx_hi, cx_lo, cy_hi, cy_lo;   // beta of the tile centre without the lens sum, relative
+                                      // to the base pixel's corner (double-float)
+  int32_t ix, iy;                     // base pixel
+  int32_t n_near, pad_;
+  float T[SHEET_TERMS][2];            // Taylor coefficients of the sheet's analytic part, t^1..
+  float near[MAX_NEAR][4];            // (z_T - c).re, .im, a_c, 0 of corners handled per ray
+};
+
+// Geometry of brute-force tile `tile` (row-major over tiles): first ray (i0, j0),
+// one past the last valid ray (i1, j1), and the lattice coordinate of its centre.
+struct TileGeo {
+  int64_t i0, j0, i1, j1;
+  double ci, cj;
+};
+__device__ __forceinline__ TileGeo tile_geo(const Geo& g, int64_t tile, int64_t ntx) {
+  TileGeo t;
+  const int64_t tx = tile % ntx, ty = tile / ntx;
+  t.i0 = tx * BR_TX;
+  t.j0 = ty * BR_TY;
+  t.i1 = min(t.i0 + (int64_t)BR_TX, g.nrx);
+  t.j1 = min(t.j0 + (int64_t)BR_TY, g.nry);
+  t.ci = 0.5 * (double)(t.i0 + t.i1);
+  t.cj = 0.5 * (double)(t.j0 + t.j1);
+  return t;
+}
+
+}  // namespace irs
+
+// ---------------------------------------------------------------- host side
+struct irs_plan {
+  irs_params p;
+  irs::Geo g;
+  // FP64 sizing (flow chart)
+  double kappa, border, lambda1, lambda2, ix0, iy0, ix, iy, circle_r;
+  int64_t n_star_suggested;
+  // brute-force tiling
+  int64_t br_ntx, br_nty, br_ntiles;
+  int br_grid;
+  // device workspace
+  void* ws;
+  size_t ws_bytes;
+  double* d_msum;          // [1] sum of masses
+  double* d_mpart;         // [MSUM_BLOCKS] partial sums
+  irs::TileRec* d_tiles;   // [br_ntiles]
+  int* d_status;           // sticky device error
+  int device;
+  int num_sms;
+  // INTERP state (irs_interp.cu)
+  void* interp;
+  // stage timing (irs_plan_set_timing)
+  int timing;
+  cudaEvent_t ev[8];
+  int64_t timed_rays;
+  int has_mag;
+};
+
+namespace irs {
+// timing event slots of irs_plan::ev
+enum { EV_START = 0, EV_PREP, EV_CELLS, EV_FAR, EV_RAY0, EV_RAY1, EV_MAG, EV_END, EV_COUNT };
+}  // namespace irs
+
+namespace irs {
+constexpr int MSUM_BLOCKS = 128;
+constexpr int MSUM_THREADS = 256;
+
+// launchers implemented in irs_brute.cu
+cudaError_t launch_mass_sum(const irs_plan_t* P, const double* mass, int64_t n, cudaStream_t s);
+cudaError_t launch_brute_setup(const irs_plan_t* P, cudaStream_t s);
+cudaError_t launch_brute_map(const irs_plan_t* P, const double* xy, const double* mass, int64_t n,
+                             int64_t row0, int64_t row1, uint32_t* counts, cudaStream_t s);
+cudaError_t launch_brute_dump(const irs_plan_t* P, const double* xy, const double* mass, int64_t n,
+                              const int64_t* idx, int64_t nidx, double* beta, int64_t* pix,
+                              cudaStream_t s);
+cudaError_t launch_magnify(const irs_plan_t* P, const uint32_t* counts, float* mag, cudaStream_t s);
+int brute_grid_size(int num_sms);
+}  // namespace irs
