@@ -155,7 +155,7 @@ typedef struct irs_timings {
   float ms_magnify;   /* magnification (0 if not requested) */
   int64_t rays;       /* rays shot by the timed map */
   int32_t valid;      /* 1 when the fields hold a measurement */
-  int32_t pad_;
+  int32_t launches;   /* kernel launches of the map */
 } irs_timings;
 
 irs_status irs_plan_set_timing(irs_plan_t* plan, int32_t enable);

@@ -138,6 +138,7 @@ irs_status run_map(irs_plan_t* P, const double* xy, const double* mass, int64_t 
   if (st != IRS_OK) return st;
   const size_t npix = (size_t)P->g.npix_x * P->g.npix_y;
   if (clear) IRS_TRY(cudaMemsetAsync(counts, 0, npix * sizeof(uint32_t), s));
+  P->launches = 2;  // mass sum
   mark(P, irs::EV_START, s);
   IRS_TRY(irs::launch_mass_sum(P, mass, n, s));
   if (P->p.method == IRS_BRUTE) {
@@ -147,6 +148,7 @@ irs_status run_map(irs_plan_t* P, const double* xy, const double* mass, int64_t 
     mark(P, irs::EV_FAR, s);
     mark(P, irs::EV_RAY0, s);
     IRS_TRY(irs::launch_brute_map(P, xy, mass, n, row0, row1, counts, s));
+    P->launches += row1 > row0 ? 2 : 1;
     mark(P, irs::EV_RAY1, s);
   } else {
     st = irs::interp_run(P, xy, mass, n, row0, row1, counts, s);
@@ -154,6 +156,7 @@ irs_status run_map(irs_plan_t* P, const double* xy, const double* mass, int64_t 
   }
   mark(P, irs::EV_MAG, s);
   if (mag) IRS_TRY(irs::launch_magnify(P, counts, mag, s));
+  if (mag) P->launches += 1;
   mark(P, irs::EV_END, s);
   P->timed_rays = (row1 - row0) * P->g.nrx;
   P->has_mag = mag != nullptr;
@@ -285,6 +288,7 @@ irs_status irs_plan_timings(irs_plan_t* P, irs_timings* out) {
   out->ms_raypass = ms(irs::EV_RAY0, irs::EV_RAY1);
   out->ms_magnify = P->has_mag ? ms(irs::EV_MAG, irs::EV_END) : 0.f;
   out->rays = P->timed_rays;
+  out->launches = P->launches;
   out->valid = 1;
   return IRS_OK;
 }

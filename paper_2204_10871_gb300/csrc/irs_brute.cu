@@ -184,6 +184,13 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
       tile = (row0 / BR_TY) * ntx + work;  // tile rows covering [row0, row1)
     } else {
       const int64_t f = idx[work];
+      if (f < 0 || f >= g.nrx * g.nry) {  // not a lattice ray: report it, touch nothing else
+        if (tid == 0) {
+          beta_out[2 * work] = beta_out[2 * work + 1] = nan("");
+          if (pix_out) pix_out[work] = -1;
+        }
+        continue;
+      }
       want_i = f % g.nrx;
       want_j = f / g.nrx;
       tile = (want_j / BR_TY) * ntx + want_i / BR_TX;
@@ -217,13 +224,28 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
       float pax[BR_R], pay[BR_R];
 #pragma unroll
       for (int r = 0; r < BR_R; ++r) pax[r] = pay[r] = 0.f;
+      // lenses in this stage, rounded up to the unroll (padding is massless)
+      const int cnt = (int)min((int64_t)BR_LT, ((n - base) + 7) & ~(int64_t)7);
 #pragma unroll 2
-      for (int jl = 0; jl < BR_LT; ++jl) {
+      for (int jl = 0; jl < cnt; ++jl) {
         const float4 L = lens_s[jl];
         const float dx = tx - L.x;
         const float dx2 = dx * dx;
+        // rows 0..BR_PAIRED-1: one reciprocal for two rows, 1/(r_a^2 r_b^2), to move
+        // work from the SFU (MUFU) to the FP32 pipe; remaining rows: one each
 #pragma unroll
-        for (int r = 0; r < BR_R; ++r) {
+        for (int r = 0; r < BR_PAIRED; r += 2) {
+          const float dya = ty[r] - L.y, dyb = ty[r + 1] - L.y;
+          const float r2a = fmaf(dya, dya, dx2), r2b = fmaf(dyb, dyb, dx2);
+          const float mR = L.z * rcp_approx(r2a * r2b);
+          const float wa = r2b * mR, wb = r2a * mR;
+          pax[r] = fmaf(wa, dx, pax[r]);
+          pay[r] = fmaf(wa, dya, pay[r]);
+          pax[r + 1] = fmaf(wb, dx, pax[r + 1]);
+          pay[r + 1] = fmaf(wb, dyb, pay[r + 1]);
+        }
+#pragma unroll
+        for (int r = BR_PAIRED; r < BR_R; ++r) {
           const float dy = ty[r] - L.y;
           const float r2 = fmaf(dy, dy, dx2);
           const float w = L.z * rcp_approx(r2);

@@ -82,6 +82,7 @@ constexpr int BR_R = 8;               // rays (rows) per thread
 constexpr int BR_TY = BR_WARPS * BR_R;
 constexpr int BR_THREADS = BR_WARPS * 32;
 constexpr int BR_LT = 256;            // lenses per shared-memory stage (= FP32 partial length)
+constexpr int BR_PAIRED = 4;          // rows per thread that share one reciprocal per two rows
 constexpr int SHEET_TERMS = 8;        // Taylor terms t^1..t^8 of the sheet's analytic part
 constexpr int MAX_NEAR = 4;           // rectangle corners evaluated per ray
 
@@ -141,6 +142,7 @@ struct irs_plan {
   cudaEvent_t ev[8];
   int64_t timed_rays;
   int has_mag;
+  int launches;  // kernel launches of the last map
 };
 
 namespace irs {

@@ -1,0 +1,41 @@
+// irs_fft.cuh -- FP64 complex power-of-two FFTs in shared memory (irs_fft.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace irs {
+
+constexpr int FFT_MAX_ELEMS = 8192;  // complex doubles per CTA line buffer (128 KB)
+constexpr int FFT_MAX_LEN = 8192;    // longest line
+
+// One batched pass of 1-D FFTs over `n_lines` lines of length L.
+struct FftLines {
+  int L, logL, B;           // line length, log2 L, lines per CTA
+  int in_len, out_len;      // valid input elements (rest zero), outputs written
+  int64_t n_lines;
+  int64_t in_line_stride, in_elem_stride, out_line_stride, out_elem_stride;
+  int64_t in_grid_stride, out_grid_stride;  // between grids of a batch (gridDim.y)
+  double scale;
+};
+
+// A padded Nx x Ny spectrum layout with its twiddle tables.
+struct Fft2d {
+  int Nx, Ny, logNx, logNy;
+  double2* tw_x;
+  double2* tw_y;
+};
+
+int ilog2_exact(int64_t n);
+cudaError_t fft_twiddles(int L, double2** d_tw);
+cudaError_t fft_setup_attributes();
+cudaError_t fft_lines(const double2* in, double2* out, FftLines d, int ngrids, const double2* tw,
+                      bool inverse, cudaStream_t s);
+// compact [ngrids][ny][nx] -> padded spectra [ngrids][Ny][Nx]
+cudaError_t fft2d_forward(const double2* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
+                          double2* spec, const Fft2d& f, int ngrids, cudaStream_t s);
+// padded spectra (overwritten) -> compact [ngrids][ny][nx], scaled by 1/(Nx Ny)
+cudaError_t fft2d_inverse(double2* spec, const Fft2d& f, int64_t nx, int64_t ny, double2* compact,
+                          int64_t out_grid_stride, int ngrids, cudaStream_t s);
+
+}  // namespace irs

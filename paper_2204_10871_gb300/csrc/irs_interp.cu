@@ -1,20 +1,855 @@
-// irs_interp.cu -- interpolated method (placeholder until the far field lands).
+// irs_interp.cu -- the interpolated method of arXiv:2204.10871, Sec. 2.4
+// ("Interpolation algorithm" and the flow chart's level-1/2/3 grids),
+// re-designed for GB300.
+//
+//  level 1  square cells of k x k rays, side h = k Delta x3 with k from the
+//           paper's Delta x1 = min(L0, min(I_x, I_y)/10), L0 = sqrt(A/N_*).
+//           Lenses are binned into cells (counting sort, CSR, deterministic
+//           order inside a cell).  A ray's "nearby lenses" are those of its own
+//           cell and the 8 neighbours; they are summed directly per ray.
+//  far      every other lens and the negative sheet are summed once per cell
+//           into a Taylor series G_C(t) = sum_k c_k t^k about the cell centre:
+//             cells at Chebyshev distance 2..W: each lens directly (P2L);
+//             beyond W: multipole moments of each cell (P2M) translated to the
+//             target cell by a convolution over the regular cell grid (M2L),
+//             evaluated with FP64 FFTs;
+//             the rectangle sheet: its analytic part g(z), whose Taylor
+//             coefficients are closed-form (rational for order >= 2).
+//           All far-field accumulation is FP64.
+//  level 2  each cell's series is re-centred on Q x Q sub-cells (the paper's
+//           level-2 grid points) with K2 terms, in shared memory per CTA.
+//  level 3  the rays: one CTA per cell; near lenses broadcast from shared
+//           memory, FP32 pair sums, sub-cell Horner, pixel, warp-aggregated
+//           atomic binning.
+//
+// Per ray, with t = z - z_C (complex) and tau = t / h:
+//   conj(beta) = B_C + (1 - kappa_s) conj(t) - gamma t - L_near(t) + sum_{k>=1} c_k tau^k
+// where B_C = (1-kappa_s) conj(z_C) - gamma z_C + c_0 (rectangle), and
+// L_near(t) = sum_near m_i / (t - t_i).  The kappa_* conj(z) parts of the
+// matrix term and of the sheet cancel exactly and never appear.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "irs_fft.cuh"
 #include "irs_interp.cuh"
 
 namespace irs {
-irs_status interp_plan(irs_plan_t* P) { (void)P; return IRS_ERR_UNSUPPORTED; }
-void interp_fill_info(const irs_plan_t* P, irs_plan_info* info) { (void)P; (void)info; }
-int64_t interp_workspace_bytes(const irs_plan_t* P) { (void)P; return 0; }
+
+namespace {
+
+constexpr int IP_KMAX = 32;        // local series terms (max)
+constexpr int IP_P = 18;           // multipole terms and local terms produced by the M2L
+constexpr int IP_Q = 8;            // level-2 sub-cells per side
+constexpr int IP_K2 = 10;          // terms of a sub-cell series
+constexpr int IP_NEAR_MAX = 2048;  // lenses of a 3x3 block held in shared memory
+constexpr int IP_THREADS = 256;
+constexpr int IP_R = 4;            // rays (rows) per thread
+constexpr int IP_MAX_CORNER = 4;
+
+constexpr int DEFAULT_K = 24;
+constexpr int DEFAULT_W = 3;
+
+struct __align__(16) CellRec {
+  float bx_hi, bx_lo, by_hi, by_lo;  // beta of the centre (without L_near) relative to the base pixel
+  int32_t ix, iy;                    // base pixel
+  int32_t n_corner, pad_;
+  float corner[IP_MAX_CORNER][4];    // (z_C - c).re, .im, a_c, 0: corners evaluated per ray
+};
+
+struct IpGeo {
+  int64_t k;           // rays per cell side
+  double h;            // cell side
+  int32_t ncx, ncy;    // cell grid
+  int32_t ox, oy;      // first ray cell
+  int32_t nrcx, nrcy;  // ray cells
+  double gx0, gy0;     // grid origin (lower-left corner of cell (0,0))
+  int K, P, W;
+};
+
+struct InterpState {
+  IpGeo ig;
+  Fft2d fft;
+  void* ws;
+  size_t ws_bytes;
+  void* lens_ws;
+  size_t lens_ws_bytes;
+  int64_t cap;
+  int32_t* cell_count;
+  int32_t* cell_start;
+  int32_t* cell_cursor;
+  int32_t* scan_blocks;
+  int32_t* lens_cell;
+  int32_t* sorted_idx;
+  float4* lens_rel;
+  double2* lens_pos;
+  double* lens_m;
+  double2* mpole;  // [P][ncells]
+  double2* spec;   // [P][Ny][Nx]
+  double2* kspec;  // [2P-1][Ny][Nx]
+  double2* conv;   // [P][ncells]
+  CellRec* recs;   // [nray cells]
+  float2* coef;    // [nray cells][K]
+  int grid_ray;
+};
+
+InterpState* S_(irs_plan_t* P) { return static_cast<InterpState*>(P->interp); }
+const InterpState* S_(const irs_plan_t* P) { return static_cast<const InterpState*>(P->interp); }
+
+// ------------------------------------------------------------ complex FP64
+struct cd {
+  double re, im;
+};
+__device__ __forceinline__ cd cmul(cd a, cd b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__device__ __forceinline__ cd crecip(cd a) {
+  const double d = a.re * a.re + a.im * a.im;
+  return {a.re / d, -a.im / d};
+}
+
+// ------------------------------------------------------------ cell lists
+__device__ __forceinline__ int cell_of(const IpGeo& ig, double x, double y) {
+  long long cx = (long long)floor((x - ig.gx0) / ig.h);
+  long long cy = (long long)floor((y - ig.gy0) / ig.h);
+  cx = cx < 0 ? 0 : (cx >= ig.ncx ? ig.ncx - 1 : cx);  // lenses off the grid: edge cell
+  cy = cy < 0 ? 0 : (cy >= ig.ncy ? ig.ncy - 1 : cy);
+  return (int)(cy * ig.ncx + cx);
+}
+
+__global__ void k_ip_count(IpGeo ig, const double2* __restrict__ xy, int64_t n,
+                           int32_t* __restrict__ lens_cell, int32_t* __restrict__ count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 p = xy[i];
+  const int c = cell_of(ig, p.x, p.y);
+  lens_cell[i] = c;
+  atomicAdd(count + c, 1);
+}
+
+// exclusive scan of int32 in three passes (block scan, scan of block sums, add)
+constexpr int SCAN_B = 1024;
+__global__ void k_scan_local(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
+                             int32_t* __restrict__ block_sums) {
+  __shared__ int32_t sh[SCAN_B];
+  const int64_t i = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+  const int32_t v = i < n ? in[i] : 0;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < SCAN_B; off <<= 1) {
+    int32_t t = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) out[i] = sh[threadIdx.x] - v;
+  if (threadIdx.x == SCAN_B - 1) block_sums[blockIdx.x] = sh[SCAN_B - 1];
+}
+__global__ void k_scan_blocks(int32_t* __restrict__ block_sums, int64_t nb, int32_t* __restrict__ total) {
+  if (threadIdx.x != 0) return;
+  int32_t s = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const int32_t v = block_sums[b];
+    block_sums[b] = s;
+    s += v;
+  }
+  *total = s;
+}
+__global__ void k_scan_add(int32_t* __restrict__ out, int64_t n, const int32_t* __restrict__ block_sums) {
+  const int64_t i = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+  if (i < n) out[i] += block_sums[blockIdx.x];
+}
+
+__global__ void k_ip_scatter(const int32_t* __restrict__ lens_cell, int64_t n,
+                             int32_t* __restrict__ cursor, int32_t* __restrict__ sorted_idx) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int pos = atomicAdd(cursor + lens_cell[i], 1);
+  sorted_idx[pos] = (int32_t)i;
+}
+
+// Insertion sort of each cell's lens indices: the order inside a cell no
+// longer depends on the atomics, so every map is bitwise reproducible.
+__global__ void k_ip_sortcells(const int32_t* __restrict__ start, int64_t ncells,
+                               int32_t* __restrict__ sorted_idx) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const int a = start[c], b = start[c + 1];
+  for (int i = a + 1; i < b; ++i) {
+    const int32_t v = sorted_idx[i];
+    int j = i - 1;
+    while (j >= a && sorted_idx[j] > v) {
+      sorted_idx[j + 1] = sorted_idx[j];
+      --j;
+    }
+    sorted_idx[j + 1] = v;
+  }
+}
+
+__global__ void k_ip_fill(IpGeo ig, const double2* __restrict__ xy, const double* __restrict__ mass,
+                          const int32_t* __restrict__ sorted_idx, const int32_t* __restrict__ lens_cell,
+                          int64_t n, float4* __restrict__ rel, double2* __restrict__ pos,
+                          double* __restrict__ m_out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int32_t i = sorted_idx[p];
+  const int c = lens_cell[i];
+  const int cx = c % ig.ncx, cy = c / ig.ncx;
+  const double zx = ig.gx0 + (cx + 0.5) * ig.h, zy = ig.gy0 + (cy + 0.5) * ig.h;
+  const double2 q = xy[i];
+  const double m = mass[i];
+  rel[p] = make_float4((float)(q.x - zx), (float)(q.y - zy), (float)m, 0.f);
+  pos[p] = q;
+  m_out[p] = m;
+}
+
+// ------------------------------------------------------------ far field
+// P2M: a_j = sum_i m_i ((z_i - z_S)/h)^j for the lenses of cell S.
+__global__ void k_ip_p2m(IpGeo ig, const int32_t* __restrict__ start, const double2* __restrict__ pos,
+                         const double* __restrict__ m, double2* __restrict__ mpole) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ncells = (int64_t)ig.ncx * ig.ncy;
+  if (c >= ncells) return;
+  const int cx = (int)(c % ig.ncx), cy = (int)(c / ig.ncx);
+  const double zx = ig.gx0 + (cx + 0.5) * ig.h, zy = ig.gy0 + (cy + 0.5) * ig.h;
+  cd a[IP_P];
+#pragma unroll
+  for (int j = 0; j < IP_P; ++j) a[j] = {0.0, 0.0};
+  const double inv_h = 1.0 / ig.h;
+  for (int p = start[c]; p < start[c + 1]; ++p) {
+    const cd d = {(pos[p].x - zx) * inv_h, (pos[p].y - zy) * inv_h};
+    cd pw = {m[p], 0.0};
+#pragma unroll
+    for (int j = 0; j < IP_P; ++j) {
+      a[j].re += pw.re;
+      a[j].im += pw.im;
+      pw = cmul(pw, d);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < IP_P; ++j) mpole[(int64_t)j * ncells + c] = make_double2(a[j].re, a[j].im);
+}
+
+// Translation kernels on the padded grid: K'_n[e] = (-e)^-(n+1) for offsets
+// e (cell units, wrapped) with Chebyshev norm > W, else 0.
+__global__ void k_ip_kernel_grid(int Nx, int Ny, int W, int nker, double2* __restrict__ kg) {
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t G = (int64_t)Nx * Ny;
+  if (f >= G) return;
+  const int ex = (int)(f % Nx), ey = (int)(f / Nx);
+  const int sx = ex < Nx / 2 ? ex : ex - Nx, sy = ey < Ny / 2 ? ey : ey - Ny;
+  const bool far = abs(sx) > W || abs(sy) > W;
+  cd inv = {0.0, 0.0};
+  if (far) inv = crecip(cd{-(double)sx, -(double)sy});
+  cd pw = inv;
+  for (int n = 0; n < nker; ++n) {
+    kg[(int64_t)n * G + f] = far ? make_double2(pw.re, pw.im) : make_double2(0.0, 0.0);
+    pw = cmul(pw, inv);
+  }
+}
+
+// Pointwise M2L in frequency space:
+//   C_k = sum_j (-1)^j binom(j+k, k) A_j Kh_{j+k},  j, k < P
+__global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, double2* __restrict__ spec,
+                                                     const double2* __restrict__ kspec) {
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= G) return;
+  cd A[IP_P], Cc[IP_P];
+#pragma unroll
+  for (int j = 0; j < IP_P; ++j) {
+    const double2 v = spec[(int64_t)j * G + f];
+    const double sgn = (j & 1) ? -1.0 : 1.0;
+    A[j] = {sgn * v.x, sgn * v.y};
+    Cc[j] = {0.0, 0.0};
+  }
+#pragma unroll
+  for (int nn = 0; nn < 2 * IP_P - 1; ++nn) {
+    const double2 kv = kspec[(int64_t)nn * G + f];
+#pragma unroll
+    for (int j = 0; j < IP_P; ++j) {
+      const int k = nn - j;
+      if (k < 0 || k >= IP_P) continue;
+      // binom(j + k, k) = binom(nn, k), folded at compile time
+      double b = 1.0;
+#pragma unroll
+      for (int q = 1; q <= k; ++q) b = b * (double)(nn - k + q) / (double)q;
+      const double tr = A[j].re * kv.x - A[j].im * kv.y, ti = A[j].re * kv.y + A[j].im * kv.x;
+      Cc[k].re += b * tr;
+      Cc[k].im += b * ti;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < IP_P; ++k) spec[(int64_t)k * G + f] = make_double2(Cc[k].re, Cc[k].im);
+}
+
+// Per ray cell: window P2L, M2L result, sheet series, centre term, base pixel.
+__global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
+                              const int32_t* __restrict__ start, const double2* __restrict__ pos,
+                              const double* __restrict__ m, const double2* __restrict__ conv,
+                              CellRec* __restrict__ recs, float2* __restrict__ coef) {
+  const int64_t rc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nrc = (int64_t)ig.nrcx * ig.nrcy;
+  if (rc >= nrc) return;
+  const int cx = (int)(rc % ig.nrcx) + ig.ox, cy = (int)(rc / ig.nrcx) + ig.oy;
+  const int64_t ncells = (int64_t)ig.ncx * ig.ncy;
+  const int64_t c = (int64_t)cy * ig.ncx + cx;
+  const double zx = ig.gx0 + (cx + 0.5) * ig.h, zy = ig.gy0 + (cy + 0.5) * ig.h;
+  const double h = ig.h, inv_h = 1.0 / h;
+  const int K = ig.K;
+
+  cd acc[IP_KMAX];  // coefficients of tau^k before the 1/h of the lens parts
+  for (int k = 0; k < K; ++k) acc[k] = {0.0, 0.0};
+  // window ring: lenses of cells at Chebyshev distance 2..W, directly
+  for (int dy = -ig.W; dy <= ig.W; ++dy) {
+    const int y = cy + dy;
+    if (y < 0 || y >= ig.ncy) continue;
+    for (int dx = -ig.W; dx <= ig.W; ++dx) {
+      if (abs(dx) <= 1 && abs(dy) <= 1) continue;
+      const int x = cx + dx;
+      if (x < 0 || x >= ig.ncx) continue;
+      const int64_t s = (int64_t)y * ig.ncx + x;
+      for (int p = start[s]; p < start[s + 1]; ++p) {
+        const cd d = {(pos[p].x - zx) * inv_h, (pos[p].y - zy) * inv_h};
+        const cd inv = crecip(d);
+        cd pw = {m[p] * inv.re, m[p] * inv.im};
+        for (int k = 0; k < K; ++k) {  // + m d^-(k+1)
+          acc[k].re += pw.re;
+          acc[k].im += pw.im;
+          pw = cmul(pw, inv);
+        }
+      }
+    }
+  }
+  // outer cells through the FFT convolution
+  for (int k = 0; k < IP_P && k < K; ++k) {
+    const double2 v = conv[(int64_t)k * ncells + c];
+    acc[k].re += v.x;
+    acc[k].im += v.y;
+  }
+  for (int k = 0; k < K; ++k) {
+    acc[k].re *= inv_h;
+    acc[k].im *= inv_h;
+  }
+
+  const double ks = g.kstar_scale * msum[0];
+  const double kap = g.kappa_s + ks;
+  CellRec r;
+  r.n_corner = 0;
+  r.pad_ = 0;
+  for (int q = 0; q < IP_MAX_CORNER; ++q) r.corner[q][0] = r.corner[q][1] = r.corner[q][2] = r.corner[q][3] = 0.f;
+  cd B;
+  if (g.plane == IRS_PLANE_CIRCLE) {
+    B = {(1.0 - g.kappa_s - g.gamma) * zx - ks * g.cx, -(1.0 - g.kappa_s + g.gamma) * zy + ks * g.cy};
+  } else {
+    // sheet: g(z) = kappa_* (z - 2 a2) + sum_c -i a_c (z - c) Log(z - c); adds g_k h^k
+    acc[0].re += ks * (zx - 2.0 * g.a2);
+    acc[0].im += ks * zy;
+    acc[1].re += ks * h;
+    const double rho = 4.0 * 0.70710678118654752 * h;
+    const double cxs[4] = {g.a1, g.a2, g.a1, g.a2};
+    const double cys[4] = {g.b1, g.b1, g.b2, g.b2};
+    const double sgn[4] = {1.0, -1.0, -1.0, 1.0};
+    for (int q = 0; q < 4; ++q) {
+      const double ac = ks / M_PI * sgn[q];
+      if (ac == 0.0) continue;
+      const cd w = {zx - cxs[q], zy - cys[q]};
+      if (hypot(w.re, w.im) < rho && r.n_corner < IP_MAX_CORNER) {
+        r.corner[r.n_corner][0] = (float)w.re;
+        r.corner[r.n_corner][1] = (float)w.im;
+        r.corner[r.n_corner][2] = (float)ac;
+        r.n_corner++;
+        continue;
+      }
+      const cd L = {0.5 * log(w.re * w.re + w.im * w.im), atan2(w.im, w.re)};
+      const cd wl = cmul(w, L);
+      acc[0].re += ac * wl.im;
+      acc[0].im -= ac * wl.re;
+      acc[1].re += ac * L.im * h;
+      acc[1].im -= ac * (L.re + 1.0) * h;
+      const cd inv = crecip(w);
+      cd pw = {inv.re * h * h, inv.im * h * h};  // h^n / w^(n-1) at n = 2
+      const cd ih = {inv.re * h, inv.im * h};
+      for (int n = 2; n < K; ++n) {
+        const double cf = ((n & 1) ? -1.0 : 1.0) / (double)(n * (n - 1));
+        acc[n].re += ac * cf * pw.im;
+        acc[n].im -= ac * cf * pw.re;
+        pw = cmul(pw, ih);
+      }
+    }
+    B = {(1.0 - g.kappa_s - g.gamma) * zx, -(1.0 - g.kappa_s + g.gamma) * zy};
+  }
+  B.re += acc[0].re;
+  B.im += acc[0].im;
+  const double m1 = (1.0 - kap - g.gamma) * zx, m2 = (1.0 - kap + g.gamma) * zy;
+  double fx = floor((m1 - g.src_x0) / g.sx), fy = floor((m2 - g.src_y0) / g.sy);
+  fx = fmin(fmax(fx, -1.0e9), 1.0e9);
+  fy = fmin(fmax(fy, -1.0e9), 1.0e9);
+  r.ix = (int32_t)fx;
+  r.iy = (int32_t)fy;
+  split_df(B.re - (g.src_x0 + fx * g.sx), r.bx_hi, r.bx_lo);
+  split_df(-B.im - (g.src_y0 + fy * g.sy), r.by_hi, r.by_lo);
+  recs[rc] = r;
+  for (int k = 0; k < K; ++k) coef[rc * K + k] = make_float2((float)acc[k].re, (float)acc[k].im);
+}
+
+// ------------------------------------------------------------ ray pass
+enum { IP_MAP = 0, IP_DUMP = 1 };
+
+struct IpRayArgs {
+  const int32_t* start;
+  const float4* rel;
+  const CellRec* recs;
+  const float2* coef;
+  uint32_t* counts;
+  int* status;
+  int64_t row0, row1;
+  int64_t rc_base;  // first ray cell of the work range
+  const int64_t* idx;
+  double* beta_out;
+  int64_t* pix_out;
+  int64_t nwork;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(IP_THREADS, 2) k_ip_ray(Geo g, IpGeo ig, IpRayArgs a) {
+  __shared__ float4 near_s[IP_NEAR_MAX];
+  __shared__ float2 sub_s[IP_Q * IP_Q][IP_K2];
+  __shared__ float2 c_s[IP_KMAX];
+  __shared__ CellRec rec_s;
+  __shared__ int blk_start[9], blk_off[10];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t k = ig.k;
+  const float hf = (float)ig.h;
+  const float inv_k = 1.0f / (float)k;
+
+  for (int64_t work = blockIdx.x; work < a.nwork; work += gridDim.x) {
+    int64_t rc, want_i = -1, want_j = -1;
+    if (MODE == IP_MAP) {
+      rc = a.rc_base + work;
+    } else {
+      const int64_t f = a.idx[work];
+      if (f < 0 || f >= g.nrx * g.nry) {  // not a lattice ray: report it, touch nothing else
+        if (tid == 0) {
+          a.beta_out[2 * work] = a.beta_out[2 * work + 1] = nan("");
+          if (a.pix_out) a.pix_out[work] = -1;
+        }
+        continue;
+      }
+      want_i = f % g.nrx;
+      want_j = f / g.nrx;
+      rc = (want_j / k) * ig.nrcx + want_i / k;
+    }
+    const int rcx = (int)(rc % ig.nrcx), rcy = (int)(rc / ig.nrcx);
+    const int cx = rcx + ig.ox, cy = rcy + ig.oy;
+    const int64_t i0 = (int64_t)rcx * k, j0 = (int64_t)rcy * k;
+    const int64_t i1 = min(i0 + k, g.nrx);
+    int64_t jlo = j0, jhi = min(j0 + k, g.nry);
+    if (MODE == IP_MAP) {
+      jlo = max(jlo, a.row0);
+      jhi = min(jhi, a.row1);
+      if (jlo >= jhi) continue;  // uniform over the CTA
+    }
+    __syncthreads();  // previous cell's shared data no longer read
+    if (tid == 0) {
+      rec_s = a.recs[rc];
+      int off = 0;
+      for (int q = 0; q < 9; ++q) {
+        const int x = cx + (q % 3) - 1, y = cy + (q / 3) - 1;
+        int s0 = 0, cnt = 0;
+        if (x >= 0 && x < ig.ncx && y >= 0 && y < ig.ncy) {
+          const int64_t s = (int64_t)y * ig.ncx + x;
+          s0 = a.start[s];
+          cnt = a.start[s + 1] - s0;
+        }
+        blk_start[q] = s0;
+        blk_off[q] = off;
+        off += cnt;
+      }
+      if (off > IP_NEAR_MAX) {
+        atomicExch(a.status, (int)IRS_ERR_OVERFLOW);
+        off = IP_NEAR_MAX;
+      }
+      blk_off[9] = off;
+    }
+    for (int q = tid; q < ig.K; q += blockDim.x) c_s[q] = a.coef[rc * ig.K + q];
+    __syncthreads();
+    const int n_near = blk_off[9];
+    for (int t = tid; t < n_near; t += blockDim.x) {
+      int q = 0;
+      while (q < 8 && t >= blk_off[q + 1]) ++q;
+      const float4 v = a.rel[blk_start[q] + (t - blk_off[q])];
+      const float ox = (float)((q % 3) - 1) * hf, oy = (float)((q / 3) - 1) * hf;
+      near_s[t] = make_float4(v.x + ox, v.y + oy, v.z, 0.f);
+    }
+    // level 2: re-centre the series on the sub-cell centres eps (cell units)
+    for (int t = tid; t < IP_Q * IP_Q * IP_K2; t += blockDim.x) {
+      const int sub = t / IP_K2, nn = t % IP_K2;
+      const float er = ((float)(sub % IP_Q) + 0.5f) / IP_Q - 0.5f;
+      const float ei = ((float)(sub / IP_Q) + 0.5f) / IP_Q - 0.5f;
+      float sr = 0.f, si = 0.f, tr = 1.f, ti = 0.f;  // term = binom(kk, nn) eps^(kk - nn)
+      for (int kk = nn; kk < ig.K; ++kk) {
+        if (kk >= 1) {
+          const float2 c = c_s[kk];
+          sr = fmaf(c.x, tr, fmaf(-c.y, ti, sr));
+          si = fmaf(c.x, ti, fmaf(c.y, tr, si));
+        }
+        const float f = (float)(kk + 1) / (float)(kk + 1 - nn);
+        const float nr = (tr * er - ti * ei) * f, ni = (tr * ei + ti * er) * f;
+        tr = nr;
+        ti = ni;
+      }
+      const float sc = powf((float)IP_Q, -(float)nn);
+      sub_s[sub][nn] = make_float2(sr * sc, si * sc);
+    }
+    __syncthreads();
+
+    for (int64_t c0 = i0; c0 < i1; c0 += 32) {
+      const int64_t col = c0 + lane;
+      const float taux = ((float)(col - i0) + 0.5f) * inv_k - 0.5f;
+      const float tx = taux * hf;
+      for (int64_t r0 = jlo + warp * IP_R; r0 < jhi; r0 += (IP_THREADS / 32) * IP_R) {
+        float tauy[IP_R], ty[IP_R], ax[IP_R], ay[IP_R];
+#pragma unroll
+        for (int r = 0; r < IP_R; ++r) {
+          tauy[r] = ((float)(r0 + r - j0) + 0.5f) * inv_k - 0.5f;
+          ty[r] = tauy[r] * hf;
+          ax[r] = ay[r] = 0.f;
+        }
+#pragma unroll 2
+        for (int q = 0; q < n_near; ++q) {
+          const float4 L = near_s[q];
+          const float dx = tx - L.x;
+          const float dx2 = dx * dx;
+#pragma unroll
+          for (int r = 0; r < IP_R; ++r) {
+            const float dy = ty[r] - L.y;
+            const float r2 = fmaf(dy, dy, dx2);
+            const float w = L.z * rcp_approx(r2);
+            ax[r] = fmaf(w, dx, ax[r]);
+            ay[r] = fmaf(w, dy, ay[r]);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < IP_R; ++r) {
+          const int64_t row = r0 + r;
+          const bool inside = col < i1 && row < jhi;
+          // sub-cell and its series in sigma = (tau - eps) Q
+          int u = (int)floorf((taux + 0.5f) * IP_Q), v = (int)floorf((tauy[r] + 0.5f) * IP_Q);
+          u = u < 0 ? 0 : (u >= IP_Q ? IP_Q - 1 : u);
+          v = v < 0 ? 0 : (v >= IP_Q ? IP_Q - 1 : v);
+          const float sgr = (taux - (((float)u + 0.5f) / IP_Q - 0.5f)) * IP_Q;
+          const float sgi = (tauy[r] - (((float)v + 0.5f) / IP_Q - 0.5f)) * IP_Q;
+          const float2* d = sub_s[v * IP_Q + u];
+          float pr = d[IP_K2 - 1].x, pi = d[IP_K2 - 1].y;
+#pragma unroll
+          for (int nn = IP_K2 - 2; nn >= 0; --nn) {
+            const float nr = fmaf(pr, sgr, fmaf(-pi, sgi, d[nn].x));
+            const float ni = fmaf(pr, sgi, fmaf(pi, sgr, d[nn].y));
+            pr = nr;
+            pi = ni;
+          }
+          for (int q = 0; q < rec_s.n_corner; ++q) {
+            const float wr = rec_s.corner[q][0] + tx, wi = rec_s.corner[q][1] + ty[r];
+            const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
+            const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
+            pr += rec_s.corner[q][2] * pli;
+            pi -= rec_s.corner[q][2] * plr;
+          }
+          const float b1 = rec_s.bx_hi + ((rec_s.bx_lo - ax[r]) + (g.lam_s1 * tx + pr));
+          const float b2 = rec_s.by_hi + ((rec_s.by_lo - ay[r]) + (g.lam_s2 * ty[r] - pi));
+          uint32_t key = 0;
+          int64_t pix = -1;
+          const bool ok = inside && pixel_from_rel(g, rec_s.ix, rec_s.iy, b1, b2, key, pix);
+          if (MODE == IP_MAP) {
+            bin_warp(a.counts, ok, key);
+          } else if (col == want_i && row == want_j) {
+            a.beta_out[2 * work] = (g.src_x0 + (double)rec_s.ix * g.sx) + (double)b1;
+            a.beta_out[2 * work + 1] = (g.src_y0 + (double)rec_s.iy * g.sy) + (double)b2;
+            if (a.pix_out) a.pix_out[work] = pix;
+          }
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ host helpers
+int64_t next_pow2(int64_t n) {
+  int64_t p = 2;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+irs_status alloc_lens_buffers(InterpState* S, int64_t cap) {
+  if (S->lens_ws) cudaFree(S->lens_ws);
+  S->lens_ws = nullptr;
+  cap = cap < 256 ? 256 : cap;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += (b + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_cell = take(sizeof(int32_t) * cap), o_sidx = take(sizeof(int32_t) * cap);
+  const size_t o_rel = take(sizeof(float4) * cap), o_pos = take(sizeof(double2) * cap);
+  const size_t o_m = take(sizeof(double) * cap);
+  if (cudaMalloc(&S->lens_ws, off) != cudaSuccess) {
+    cudaGetLastError();
+    S->lens_ws = nullptr;
+    S->cap = 0;
+    return IRS_ERR_OOM;
+  }
+  char* b = static_cast<char*>(S->lens_ws);
+  S->lens_cell = reinterpret_cast<int32_t*>(b + o_cell);
+  S->sorted_idx = reinterpret_cast<int32_t*>(b + o_sidx);
+  S->lens_rel = reinterpret_cast<float4*>(b + o_rel);
+  S->lens_pos = reinterpret_cast<double2*>(b + o_pos);
+  S->lens_m = reinterpret_cast<double*>(b + o_m);
+  S->lens_ws_bytes = off;
+  S->cap = cap;
+  return IRS_OK;
+}
+
+void mark(irs_plan_t* P, int slot, cudaStream_t s) {
+  if (P->timing) cudaEventRecord(P->ev[slot], s);
+}
+
+#define IP_TRY(expr)                                                     \
+  do {                                                                   \
+    cudaError_t e_ = (expr);                                             \
+    if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? IRS_ERR_OOM : IRS_ERR_CUDA; \
+  } while (0)
+
+// kernel launches of one map, reported through irs_plan_timings
+int far_launches(int64_t n) { return (n > 0 ? 4 : 0) + 3 + 1 + 2 + 1 + 2 + 1; }
+
+irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* mass, int64_t n,
+                               cudaStream_t s) {
+  InterpState* S = S_(P);
+  const IpGeo& ig = S->ig;
+  const int64_t ncells = (int64_t)ig.ncx * ig.ncy;
+  if (n > S->cap) {
+    cudaStreamSynchronize(s);
+    irs_status st = alloc_lens_buffers(S, n + n / 4);
+    if (st != IRS_OK) return st;
+  }
+  const double2* xy2 = reinterpret_cast<const double2*>(xy);
+  IP_TRY(cudaMemsetAsync(S->cell_count, 0, sizeof(int32_t) * ncells, s));
+  if (n > 0) k_ip_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ig, xy2, n, S->lens_cell, S->cell_count);
+  const int64_t nb = (ncells + SCAN_B - 1) / SCAN_B;
+  k_scan_local<<<(unsigned)nb, SCAN_B, 0, s>>>(S->cell_count, S->cell_start, ncells, S->scan_blocks);
+  k_scan_blocks<<<1, 32, 0, s>>>(S->scan_blocks, nb, S->cell_start + ncells);
+  k_scan_add<<<(unsigned)nb, SCAN_B, 0, s>>>(S->cell_start, ncells, S->scan_blocks);
+  IP_TRY(cudaGetLastError());
+  if (n > 0) {
+    IP_TRY(cudaMemcpyAsync(S->cell_cursor, S->cell_start, sizeof(int32_t) * ncells,
+                           cudaMemcpyDeviceToDevice, s));
+    k_ip_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S->lens_cell, n, S->cell_cursor, S->sorted_idx);
+    k_ip_sortcells<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(S->cell_start, ncells, S->sorted_idx);
+    k_ip_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ig, xy2, mass, S->sorted_idx, S->lens_cell, n,
+                                                         S->lens_rel, S->lens_pos, S->lens_m);
+  }
+  IP_TRY(cudaGetLastError());
+  mark(P, EV_CELLS, s);
+  // far field
+  k_ip_p2m<<<(unsigned)((ncells + 127) / 128), 128, 0, s>>>(ig, S->cell_start, S->lens_pos, S->lens_m, S->mpole);
+  IP_TRY(cudaGetLastError());
+  IP_TRY(fft2d_forward(S->mpole, ig.ncx, ig.ncy, ncells, S->spec, S->fft, ig.P, s));
+  const int64_t G = (int64_t)S->fft.Nx * S->fft.Ny;
+  k_ip_m2l_freq<<<(unsigned)((G + 127) / 128), 128, 0, s>>>(G, S->spec, S->kspec);
+  IP_TRY(cudaGetLastError());
+  IP_TRY(fft2d_inverse(S->spec, S->fft, ig.ncx, ig.ncy, S->conv, ncells, ig.P, s));
+  const int64_t nrc = (int64_t)ig.nrcx * ig.nrcy;
+  k_ip_finalize<<<(unsigned)((nrc + 63) / 64), 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start, S->lens_pos,
+                                                          S->lens_m, S->conv, S->recs, S->coef);
+  IP_TRY(cudaGetLastError());
+  mark(P, EV_FAR, s);
+  return IRS_OK;
+}
+
+IpRayArgs ray_args(irs_plan_t* P) {
+  InterpState* S = S_(P);
+  IpRayArgs a{};
+  a.start = S->cell_start;
+  a.rel = S->lens_rel;
+  a.recs = S->recs;
+  a.coef = S->coef;
+  a.status = P->d_status;
+  return a;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ entry points
+irs_status interp_plan(irs_plan_t* P) {
+  InterpState* S = new (std::nothrow) InterpState();
+  if (!S) return IRS_ERR_OOM;
+  memset(S, 0, sizeof(*S));
+  P->interp = S;
+  IpGeo& ig = S->ig;
+  const irs_params& p = P->p;
+  const Geo& g = P->g;
+  const double Ix = P->ix, Iy = P->iy;
+  int64_t nstar = p.n_star > 0 ? p.n_star : P->n_star_suggested;
+  if (nstar < 1) nstar = 1;
+  // level-1 resolution, flow chart: Delta x1 = min(L0, min(I_x, I_y)/10)
+  const double L0 = sqrt(Ix * Iy / (double)nstar);
+  double dx1 = fmin(L0, fmin(Ix, Iy) / 10.0) * (p.cell_mult > 0 ? p.cell_mult : 1.0);
+  int64_t k = (int64_t)ceil(dx1 / g.dx3 - 1e-9);
+  if (k < 4) k = 4;
+  if (k > (int64_t)1 << 20) return IRS_ERR_OVERFLOW;
+  ig.k = k;
+  ig.h = (double)k * g.dx3;
+  ig.nrcx = (int32_t)((g.nrx + k - 1) / k);
+  ig.nrcy = (int32_t)((g.nry + k - 1) / k);
+  // lens region: the rectangle, or the circumscribed circle's bounding box
+  int64_t ox = 0, oy = 0, ex = 0, ey = 0;
+  if (p.plane == IRS_PLANE_CIRCLE) {
+    const double R = P->circle_r;
+    ox = (int64_t)ceil((g.a1 - (g.cx - R)) / ig.h);
+    oy = (int64_t)ceil((g.b1 - (g.cy - R)) / ig.h);
+    ex = (int64_t)ceil(((g.cx + R) - (g.a1 + ig.nrcx * ig.h)) / ig.h);
+    ey = (int64_t)ceil(((g.cy + R) - (g.b1 + ig.nrcy * ig.h)) / ig.h);
+    ox = ox < 0 ? 0 : ox;
+    oy = oy < 0 ? 0 : oy;
+    ex = ex < 0 ? 0 : ex;
+    ey = ey < 0 ? 0 : ey;
+  }
+  const int64_t ncx = ox + ig.nrcx + ex, ncy = oy + ig.nrcy + ey;
+  if (ncx > FFT_MAX_LEN / 2 || ncy > FFT_MAX_LEN / 2) return IRS_ERR_OVERFLOW;
+  ig.ncx = (int32_t)ncx;
+  ig.ncy = (int32_t)ncy;
+  ig.ox = (int32_t)ox;
+  ig.oy = (int32_t)oy;
+  ig.gx0 = g.a1 - (double)ox * ig.h;
+  ig.gy0 = g.b1 - (double)oy * ig.h;
+  ig.K = p.far_order > 0 ? p.far_order : DEFAULT_K;
+  ig.W = p.window > 0 ? p.window : DEFAULT_W;
+  ig.P = IP_P;
+  if (ig.K > IP_KMAX || ig.K < IP_K2) return IRS_ERR_ARG;
+  if (ig.W < 1) ig.W = 1;
+
+  Fft2d& f = S->fft;
+  f.Nx = (int)next_pow2(2 * ncx - 1);
+  f.Ny = (int)next_pow2(2 * ncy - 1);
+  f.logNx = ilog2_exact(f.Nx);
+  f.logNy = ilog2_exact(f.Ny);
+  if (fft_setup_attributes() != cudaSuccess) return IRS_ERR_CUDA;
+  if (fft_twiddles(f.Nx, &f.tw_x) != cudaSuccess) return IRS_ERR_OOM;
+  if (fft_twiddles(f.Ny, &f.tw_y) != cudaSuccess) return IRS_ERR_OOM;
+
+  const int64_t ncells = ncx * ncy, nrc = (int64_t)ig.nrcx * ig.nrcy;
+  const int64_t G = (int64_t)f.Nx * f.Ny;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += (b + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_cnt = take(sizeof(int32_t) * ncells), o_start = take(sizeof(int32_t) * (ncells + 1));
+  const size_t o_cur = take(sizeof(int32_t) * ncells);
+  const size_t o_sb = take(sizeof(int32_t) * ((ncells + SCAN_B - 1) / SCAN_B + 1));
+  const size_t o_mp = take(sizeof(double2) * ig.P * ncells), o_conv = take(sizeof(double2) * ig.P * ncells);
+  const size_t o_spec = take(sizeof(double2) * ig.P * G), o_kspec = take(sizeof(double2) * (2 * ig.P - 1) * G);
+  const size_t o_rec = take(sizeof(CellRec) * nrc), o_coef = take(sizeof(float2) * ig.K * nrc);
+  if (cudaMalloc(&S->ws, off) != cudaSuccess) {
+    cudaGetLastError();
+    S->ws = nullptr;
+    return IRS_ERR_OOM;
+  }
+  S->ws_bytes = off;
+  char* b = static_cast<char*>(S->ws);
+  S->cell_count = reinterpret_cast<int32_t*>(b + o_cnt);
+  S->cell_start = reinterpret_cast<int32_t*>(b + o_start);
+  S->cell_cursor = reinterpret_cast<int32_t*>(b + o_cur);
+  S->scan_blocks = reinterpret_cast<int32_t*>(b + o_sb);
+  S->mpole = reinterpret_cast<double2*>(b + o_mp);
+  S->conv = reinterpret_cast<double2*>(b + o_conv);
+  S->spec = reinterpret_cast<double2*>(b + o_spec);
+  S->kspec = reinterpret_cast<double2*>(b + o_kspec);
+  S->recs = reinterpret_cast<CellRec*>(b + o_rec);
+  S->coef = reinterpret_cast<float2*>(b + o_coef);
+  irs_status st = alloc_lens_buffers(S, nstar + nstar / 4 + 256);
+  if (st != IRS_OK) return st;
+  // translation kernels and their spectra, once per plan
+  const int nker = 2 * ig.P - 1;
+  k_ip_kernel_grid<<<(unsigned)((G + 255) / 256), 256>>>(f.Nx, f.Ny, ig.W, nker, S->kspec);
+  if (cudaGetLastError() != cudaSuccess) return IRS_ERR_CUDA;
+  if (fft2d_forward(S->kspec, f.Nx, f.Ny, G, S->kspec, f, nker, 0) != cudaSuccess) return IRS_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return IRS_ERR_CUDA;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP>, IP_THREADS, 0);
+  S->grid_ray = P->num_sms * (per_sm > 0 ? per_sm : 1);
+  return IRS_OK;
+}
+
+void interp_fill_info(const irs_plan_t* P, irs_plan_info* info) {
+  const InterpState* S = S_(P);
+  if (!S) return;
+  info->cell_x = info->cell_y = S->ig.h;
+  info->ncell_x = S->ig.ncx;
+  info->ncell_y = S->ig.ncy;
+  info->rays_per_cell_x = info->rays_per_cell_y = (int32_t)S->ig.k;
+  info->far_order = S->ig.K;
+  info->window = S->ig.W;
+}
+
+int64_t interp_workspace_bytes(const irs_plan_t* P) {
+  const InterpState* S = S_(P);
+  return S ? (int64_t)(S->ws_bytes + S->lens_ws_bytes) : 0;
+}
+
 irs_status interp_run(irs_plan_t* P, const double* xy, const double* mass, int64_t n, int64_t row0,
                       int64_t row1, uint32_t* counts, cudaStream_t s) {
-  (void)P; (void)xy; (void)mass; (void)n; (void)row0; (void)row1; (void)counts; (void)s;
-  return IRS_ERR_UNSUPPORTED;
+  InterpState* S = S_(P);
+  mark(P, EV_PREP, s);
+  irs_status st = build_cells_and_far(P, xy, mass, n, s);
+  if (st != IRS_OK) return st;
+  mark(P, EV_RAY0, s);
+  P->launches += far_launches(n) + (row1 > row0 ? 1 : 0);
+  if (row1 > row0) {
+    IpRayArgs a = ray_args(P);
+    a.counts = counts;
+    a.row0 = row0;
+    a.row1 = row1;
+    const int64_t k = S->ig.k;
+    const int64_t rc0 = (row0 / k) * S->ig.nrcx, rc1 = ((row1 + k - 1) / k) * S->ig.nrcx;
+    a.rc_base = rc0;
+    a.nwork = rc1 - rc0;
+    const int64_t grid = (rc1 - rc0) < S->grid_ray ? (rc1 - rc0) : S->grid_ray;
+    k_ip_ray<IP_MAP><<<(unsigned)grid, IP_THREADS, 0, s>>>(P->g, S->ig, a);
+    if (cudaGetLastError() != cudaSuccess) return IRS_ERR_CUDA;
+  }
+  mark(P, EV_RAY1, s);
+  return IRS_OK;
 }
+
 irs_status interp_shoot_rays(irs_plan_t* P, const double* xy, const double* mass, int64_t n,
                              const int64_t* idx, int64_t nidx, double* beta, int64_t* pix,
                              cudaStream_t s) {
-  (void)P; (void)xy; (void)mass; (void)n; (void)idx; (void)nidx; (void)beta; (void)pix; (void)s;
-  return IRS_ERR_UNSUPPORTED;
+  InterpState* S = S_(P);
+  irs_status st = build_cells_and_far(P, xy, mass, n, s);
+  if (st != IRS_OK) return st;
+  IpRayArgs a = ray_args(P);
+  a.idx = idx;
+  a.beta_out = beta;
+  a.pix_out = pix;
+  a.nwork = nidx;
+  const int64_t grid = nidx < S->grid_ray ? nidx : S->grid_ray;
+  k_ip_ray<IP_DUMP><<<(unsigned)grid, IP_THREADS, 0, s>>>(P->g, S->ig, a);
+  return cudaGetLastError() == cudaSuccess ? IRS_OK : IRS_ERR_CUDA;
 }
-void interp_destroy(irs_plan_t* P) { (void)P; }
+
+void interp_destroy(irs_plan_t* P) {
+  InterpState* S = S_(P);
+  if (!S) return;
+  if (S->ws) cudaFree(S->ws);
+  if (S->lens_ws) cudaFree(S->lens_ws);
+  if (S->fft.tw_x) cudaFree(S->fft.tw_x);
+  if (S->fft.tw_y) cudaFree(S->fft.tw_y);
+  delete S;
+  P->interp = nullptr;
+}
+
 }  // namespace irs

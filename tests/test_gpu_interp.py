@@ -1,0 +1,174 @@
+"""Parity of the interpolated CUDA method (cell lists + far-field series) with
+the FP64 oracle and with the GPU brute force.
+
+Bars: sampled deflections within 1e-5 theta_E of the oracle (rays farther than
+0.1 theta_E from every lens); maps within 1e-4 misbinned rays of the oracle on
+small workloads; per-pixel magnification relative RMS <= 1e-3 against the
+brute force over pixels with >= 100 rays.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_10871_gb300 import irs
+from gpu_common import (DEFLECTION_TOL, MISBIN_TOL, NEAR_LENS, lenses_for, misbinned,
+                        nearest_lens_distance, params_pair, ray_positions, require_gpu, to_dev)
+
+pytestmark = pytest.mark.gpu
+
+REL_RMS_TOL = 1e-3
+
+
+def rel_rms(mu_test, mu_ref, counts_ref, min_rays=100):
+    sel = counts_ref >= min_rays
+    assert sel.sum() > 0
+    r = (mu_test[sel] - mu_ref[sel]) / mu_ref[sel]
+    return float(np.sqrt(np.mean(r * r))), int(sel.sum())
+
+
+def sampled_check(torch, cfg, n, shape, seed, nsamp=3000, kappa_rescale=True, plane=0, **kw):
+    po, pl = params_pair(*cfg, plane=plane, method=irs.IRS_INTERP, **kw)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, n, shape=shape, seed=seed, plane=plane,
+                       kappa_star=cfg[0] if kappa_rescale else None)
+    rng = np.random.default_rng(seed + 17)
+    idx = rng.integers(0, qo.n_rays, nsamp).astype(np.int64)
+    _, bo, pixo = oracle.shoot_rays(po, qo, xy, m, idx)
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        beta, pix = plan.shoot_rays(dxy, dm, torch.from_numpy(idx).cuda())
+        plan.sync()
+        info = plan.info
+    bg, pg = beta.cpu().numpy(), pix.cpu().numpy()
+    err = np.abs(bg - bo).max(1)
+    far = nearest_lens_distance(xy, ray_positions(qo, idx)) > NEAR_LENS
+    return err, far, pg, pixo, info
+
+
+C1 = (0.3, 0.0, 0.3, (-2.5, 2.5, -2.5, 2.5), 128, 25.0)
+C2 = (0.45, 0.0, 0.45, (-10.0, 10.0, -10.0, 10.0), 2000, 100.0)
+
+
+def test_c1_sampled_deflection():
+    torch = require_gpu()
+    err, far, pg, pixo, info = sampled_check(torch, C1, 150, "equal", 1)
+    assert info.ncell_x > 3 and info.ncell_y > 3
+    assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
+    assert np.mean(pg != pixo) <= 2e-3
+
+
+def test_c1_map_vs_oracle():
+    torch = require_gpu()
+    po, pl = params_pair(*C1, method=irs.IRS_INTERP)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 150, seed=1, kappa_star=0.3)
+    co, _, landed = oracle.make_map(po, qo, xy, m)
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        counts, mag = plan.make_map(dxy, dm)
+        plan.sync()
+    bad = misbinned(co, counts.cpu().numpy())
+    assert bad <= MISBIN_TOL * landed, f"{bad} of {landed} rays binned differently"
+
+
+@pytest.mark.parametrize("cfg,n,shape", [
+    ((0.45, 0.05, 0.1, (-2.0, 2.0, -2.0, 2.0), 64, 16.0), 400, "uniform"),
+    ((0.2, 0.3, -0.35, (-1.0, 3.0, -0.5, 1.5), (48, 24), 9.0), 300, "salpeter"),
+    ((0.6, 0.0, 0.05, (-1.5, 1.5, -1.5, 1.5), 32, 25.0), 900, "equal"),
+])
+def test_dense_fields_sampled(cfg, n, shape):
+    """Fields with many cells beyond the direct window, so the FFT far field
+    carries most lenses; off-centre and non-square source regions."""
+    torch = require_gpu()
+    err, far, pg, pixo, info = sampled_check(torch, cfg, n, shape, seed=9)
+    assert info.ncell_x >= 8 or info.ncell_y >= 8
+    assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
+
+
+def test_c2_full_size_sampled():
+    """The full mid-size workload (1e5 Salpeter lenses, 1.1e10 rays): sampled
+    rays against the oracle, for the interpolated method and the brute force."""
+    torch = require_gpu()
+    err, far, pg, pixo, info = sampled_check(torch, C2, 100000, "salpeter", seed=2, nsamp=1500)
+    assert info.n_rays > 1e10
+    assert err[far].max() <= DEFLECTION_TOL, f"interp max deflection error {err[far].max():.3e}"
+    po, pl = params_pair(*C2, method=irs.IRS_BRUTE)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 100000, shape="salpeter", seed=2, kappa_star=C2[0])
+    rng = np.random.default_rng(2 + 17)
+    idx = rng.integers(0, qo.n_rays, 300).astype(np.int64)
+    _, bo, _ = oracle.shoot_rays(po, qo, xy, m, idx)
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        beta, _ = plan.shoot_rays(dxy, dm, torch.from_numpy(idx).cuda())
+        plan.sync()
+    e = np.abs(beta.cpu().numpy() - bo).max(1)
+    farb = nearest_lens_distance(xy, ray_positions(qo, idx)) > NEAR_LENS
+    assert e[farb].max() <= DEFLECTION_TOL, f"brute max deflection error {e[farb].max():.3e}"
+
+
+def test_c2_band_interp_vs_brute():
+    """Per-pixel magnification of the interpolated method against the brute
+    force on the same band of lattice rows of the full mid-size workload."""
+    torch = require_gpu()
+    po, pl_b = params_pair(*C2, method=irs.IRS_BRUTE)
+    _, pl_i = params_pair(*C2, method=irs.IRS_INTERP)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 100000, shape="salpeter", seed=2, kappa_star=C2[0])
+    dxy, dm = to_dev(torch, xy, m)
+    rows = (qo.nry // 2 - 256, qo.nry // 2 + 256)
+    maps = []
+    for pl in (pl_b, pl_i):
+        with irs.Plan(pl) as plan:
+            c = torch.zeros((2000, 2000), dtype=torch.uint32, device="cuda")
+            irs.irs_make_map_rows(plan.handle, dxy, dm, rows[0], rows[1], c)
+            plan.sync()
+            maps.append(c.cpu().numpy())
+    cb, ci = maps
+    rms, npx = rel_rms(ci.astype(np.float64), cb.astype(np.float64), cb)
+    assert npx > 1000
+    assert rms <= REL_RMS_TOL, f"rel RMS {rms:.3e} over {npx} pixels"
+
+
+def test_interp_edge_cases():
+    """No lenses; a lens count that is not a multiple of anything; circular
+    plane (cell grid over the circle's bounding box); repeat determinism."""
+    torch = require_gpu()
+    cfg = (0.3, 0.1, 0.2, (-1.0, 1.0, -1.0, 1.0), 40, 16.0)
+    po, pl = params_pair(*cfg, method=irs.IRS_INTERP)
+    qo = oracle.size(po)
+    co, _, landed = oracle.make_map(po, qo, np.zeros((0, 2)), np.zeros(0))
+    with irs.Plan(pl) as plan:
+        e = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
+        counts, _ = plan.make_map(e, torch.zeros(0, dtype=torch.float64, device="cuda"))
+        plan.sync()
+    assert misbinned(co, counts.cpu().numpy()) <= max(2, MISBIN_TOL * landed)
+
+    err, far, _, _, _ = sampled_check(torch, cfg, 97, "uniform", seed=4, plane=irs.IRS_PLANE_CIRCLE)
+    assert err[far].max() <= DEFLECTION_TOL
+
+    xy, m = lenses_for(qo, 123, seed=6, kappa_star=cfg[0])
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        a, _ = plan.make_map(dxy, dm)
+        b, _ = plan.make_map(dxy, dm)
+        plan.sync()
+    assert torch.equal(a, b)
+
+
+def test_chunked_rows_add_up():
+    """irs_make_map_rows over disjoint bands sums to the full map."""
+    torch = require_gpu()
+    cfg = (0.3, 0.1, 0.2, (-1.0, 1.0, -1.0, 1.0), 40, 16.0)
+    po, pl = params_pair(*cfg, method=irs.IRS_INTERP)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 200, seed=8, kappa_star=cfg[0])
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        full, _ = plan.make_map(dxy, dm)
+        acc = torch.zeros_like(full)
+        ny = plan.info.n_rays_y
+        for r0, r1 in [(0, 77), (77, ny // 2), (ny // 2, ny)]:
+            irs.irs_make_map_rows(plan.handle, dxy, dm, r0, r1, acc)
+        plan.sync()
+    assert torch.equal(full, acc)
