@@ -34,13 +34,15 @@ bool finite_all(const irs_params* p) {
   return true;
 }
 
+}  // namespace
+
 // Sizing, flow chart of Sec. 2.4:
 //   P = 10 sqrt(kappa_*)                      ("Protective Border")
 //   I_x = (S_x + 2P)/|1 - kappa - gamma|, I_y = (S_y + 2P)/|1 - kappa + gamma|
 //   Delta x3 = sqrt(s_x s_y / N_av), N_av rays per unlensed source pixel;
 //   the plane is widened to a whole number of rays per side and centred on
 //   the image of the source-region centre under the mean lens map.
-irs_status size_plane(irs_plan_t* P) {
+irs_status irs::size_plane(irs_plan_t* P) {
   const irs_params& p = P->p;
   P->kappa = p.kappa_s + p.kappa_star;
   P->border = p.border < 0 ? 10.0 * sqrt(p.kappa_star) : p.border;
@@ -87,6 +89,8 @@ irs_status size_plane(irs_plan_t* P) {
   }
   return IRS_OK;
 }
+
+namespace {
 
 irs_status alloc_workspace(irs_plan_t* P) {
   P->br_ntx = (P->g.nrx + irs::BR_TX - 1) / irs::BR_TX;
@@ -203,7 +207,7 @@ irs_status irs_plan(const irs_params* params, void* stream, irs_plan_t** out) {
   if (!P) return IRS_ERR_OOM;
   memset(P, 0, sizeof(*P));
   P->p = p;
-  irs_status st = size_plane(P);
+  irs_status st = irs::size_plane(P);
   if (st == IRS_OK && cudaGetDevice(&P->device) != cudaSuccess) st = IRS_ERR_CUDA;
   if (st == IRS_OK &&
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess)

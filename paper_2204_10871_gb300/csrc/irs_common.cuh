@@ -75,6 +75,18 @@ __device__ __forceinline__ bool pixel_from_rel(const Geo& g, int32_t ix, int32_t
   return true;
 }
 
+// Pixel of a ray in 32-bit arithmetic: the range test is done on the floored
+// float offsets against the cell's base pixel (lo = -base, hi = npix - base),
+// so NaN / Inf / far-off rays fail it before any conversion.
+__device__ __forceinline__ bool pixel_fast(float brel1, float brel2, float inv_sx, float inv_sy,
+                                           float lo1, float hi1, float lo2, float hi2, int32_t ix,
+                                           int32_t iy, int32_t npix_x, uint32_t& key) {
+  const float f1 = floorf(brel1 * inv_sx), f2 = floorf(brel2 * inv_sy);
+  const bool ok = (f1 >= lo1) && (f1 < hi1) && (f2 >= lo2) && (f2 < hi2);
+  key = ok ? (uint32_t)((iy + (int32_t)f2) * npix_x + (ix + (int32_t)f1)) : 0u;
+  return ok;
+}
+
 // ---------------------------------------------------------------- brute force
 constexpr int BR_TX = 32;             // tile columns: one per lane
 constexpr int BR_WARPS = 8;           // warps per CTA
@@ -164,4 +176,6 @@ cudaError_t launch_brute_dump(const irs_plan_t* P, const double* xy, const doubl
                               cudaStream_t s);
 cudaError_t launch_magnify(const irs_plan_t* P, const uint32_t* counts, float* mag, cudaStream_t s);
 int brute_grid_size(int num_sms);
+// FP64 sizing of the plane and lattice (irs_api.cu)
+irs_status size_plane(irs_plan_t* P);
 }  // namespace irs

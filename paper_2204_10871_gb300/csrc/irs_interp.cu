@@ -42,10 +42,11 @@ namespace {
 constexpr int IP_KMAX = 32;        // local series terms (max)
 constexpr int IP_P = 18;           // multipole terms and local terms produced by the M2L
 constexpr int IP_Q = 8;            // level-2 sub-cells per side
-constexpr int IP_K2 = 10;          // terms of a sub-cell series
+constexpr int IP_K2 = 8;           // terms of a sub-cell series
 constexpr int IP_NEAR_MAX = 2048;  // lenses of a 3x3 block held in shared memory
 constexpr int IP_THREADS = 256;
-constexpr int IP_R = 4;            // rays (rows) per thread
+constexpr int IP_R = 8;            // rays (rows) per thread
+constexpr int IP_WARPS = IP_THREADS / 32;
 constexpr int IP_MAX_CORNER = 4;
 
 constexpr int DEFAULT_K = 24;
@@ -504,70 +505,79 @@ __global__ void __launch_bounds__(IP_THREADS, 2) k_ip_ray(Geo g, IpGeo ig, IpRay
     }
     __syncthreads();
 
-    for (int64_t c0 = i0; c0 < i1; c0 += 32) {
-      const int64_t col = c0 + lane;
+    // base-pixel range of this cell for the 32-bit pixel test
+    const float lo1 = (float)(-rec_s.ix), hi1 = (float)(g.npix_x - rec_s.ix);
+    const float lo2 = (float)(-rec_s.iy), hi2 = (float)(g.npix_y - rec_s.iy);
+    // work units (32-column strip x IP_R-row group), dealt round-robin to warps
+    const int nstrip = (int)((i1 - i0 + 31) / 32);
+    const int nrg = (int)((jhi - jlo + IP_R - 1) / IP_R);
+    const int nunit = nstrip * nrg;
+    for (int unit = warp; unit < nunit; unit += IP_WARPS) {
+      const int st = unit % nstrip, rg = unit / nstrip;
+      const int64_t col = i0 + (int64_t)st * 32 + lane;
+      const int64_t r0 = jlo + (int64_t)rg * IP_R;
       const float taux = ((float)(col - i0) + 0.5f) * inv_k - 0.5f;
       const float tx = taux * hf;
-      for (int64_t r0 = jlo + warp * IP_R; r0 < jhi; r0 += (IP_THREADS / 32) * IP_R) {
-        float tauy[IP_R], ty[IP_R], ax[IP_R], ay[IP_R];
+      int u = (int)floorf((taux + 0.5f) * IP_Q);
+      u = u < 0 ? 0 : (u >= IP_Q ? IP_Q - 1 : u);
+      const float sgr = (taux - (((float)u + 0.5f) / IP_Q - 0.5f)) * IP_Q;
+      float ty[IP_R], ax[IP_R], ay[IP_R];
 #pragma unroll
-        for (int r = 0; r < IP_R; ++r) {
-          tauy[r] = ((float)(r0 + r - j0) + 0.5f) * inv_k - 0.5f;
-          ty[r] = tauy[r] * hf;
-          ax[r] = ay[r] = 0.f;
-        }
+      for (int r = 0; r < IP_R; ++r) {
+        ty[r] = (((float)(r0 + r - j0) + 0.5f) * inv_k - 0.5f) * hf;
+        ax[r] = ay[r] = 0.f;
+      }
 #pragma unroll 2
-        for (int q = 0; q < n_near; ++q) {
-          const float4 L = near_s[q];
-          const float dx = tx - L.x;
-          const float dx2 = dx * dx;
-#pragma unroll
-          for (int r = 0; r < IP_R; ++r) {
-            const float dy = ty[r] - L.y;
-            const float r2 = fmaf(dy, dy, dx2);
-            const float w = L.z * rcp_approx(r2);
-            ax[r] = fmaf(w, dx, ax[r]);
-            ay[r] = fmaf(w, dy, ay[r]);
-          }
-        }
+      for (int q = 0; q < n_near; ++q) {
+        const float4 L = near_s[q];
+        const float dx = tx - L.x;
+        const float dx2 = dx * dx;
 #pragma unroll
         for (int r = 0; r < IP_R; ++r) {
-          const int64_t row = r0 + r;
-          const bool inside = col < i1 && row < jhi;
-          // sub-cell and its series in sigma = (tau - eps) Q
-          int u = (int)floorf((taux + 0.5f) * IP_Q), v = (int)floorf((tauy[r] + 0.5f) * IP_Q);
-          u = u < 0 ? 0 : (u >= IP_Q ? IP_Q - 1 : u);
-          v = v < 0 ? 0 : (v >= IP_Q ? IP_Q - 1 : v);
-          const float sgr = (taux - (((float)u + 0.5f) / IP_Q - 0.5f)) * IP_Q;
-          const float sgi = (tauy[r] - (((float)v + 0.5f) / IP_Q - 0.5f)) * IP_Q;
-          const float2* d = sub_s[v * IP_Q + u];
-          float pr = d[IP_K2 - 1].x, pi = d[IP_K2 - 1].y;
+          const float dy = ty[r] - L.y;
+          const float r2 = fmaf(dy, dy, dx2);
+          const float w = L.z * rcp_approx(r2);
+          ax[r] = fmaf(w, dx, ax[r]);
+          ay[r] = fmaf(w, dy, ay[r]);
+        }
+      }
 #pragma unroll
-          for (int nn = IP_K2 - 2; nn >= 0; --nn) {
-            const float nr = fmaf(pr, sgr, fmaf(-pi, sgi, d[nn].x));
-            const float ni = fmaf(pr, sgi, fmaf(pi, sgr, d[nn].y));
-            pr = nr;
-            pi = ni;
-          }
-          for (int q = 0; q < rec_s.n_corner; ++q) {
-            const float wr = rec_s.corner[q][0] + tx, wi = rec_s.corner[q][1] + ty[r];
-            const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
-            const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
-            pr += rec_s.corner[q][2] * pli;
-            pi -= rec_s.corner[q][2] * plr;
-          }
-          const float b1 = rec_s.bx_hi + ((rec_s.bx_lo - ax[r]) + (g.lam_s1 * tx + pr));
-          const float b2 = rec_s.by_hi + ((rec_s.by_lo - ay[r]) + (g.lam_s2 * ty[r] - pi));
-          uint32_t key = 0;
-          int64_t pix = -1;
-          const bool ok = inside && pixel_from_rel(g, rec_s.ix, rec_s.iy, b1, b2, key, pix);
-          if (MODE == IP_MAP) {
-            bin_warp(a.counts, ok, key);
-          } else if (col == want_i && row == want_j) {
-            a.beta_out[2 * work] = (g.src_x0 + (double)rec_s.ix * g.sx) + (double)b1;
-            a.beta_out[2 * work + 1] = (g.src_y0 + (double)rec_s.iy * g.sy) + (double)b2;
-            if (a.pix_out) a.pix_out[work] = pix;
-          }
+      for (int r = 0; r < IP_R; ++r) {
+        const int64_t row = r0 + r;
+        const bool inside = col < i1 && row < jhi;
+        // sub-cell and its series in sigma = (tau - eps) Q
+        const float tauy = ((float)(row - j0) + 0.5f) * inv_k - 0.5f;
+        int v = (int)floorf((tauy + 0.5f) * IP_Q);
+        v = v < 0 ? 0 : (v >= IP_Q ? IP_Q - 1 : v);
+        const float sgi = (tauy - (((float)v + 0.5f) / IP_Q - 0.5f)) * IP_Q;
+        const float2* d = sub_s[v * IP_Q + u];
+        float pr = d[IP_K2 - 1].x, pi = d[IP_K2 - 1].y;
+#pragma unroll
+        for (int nn = IP_K2 - 2; nn >= 0; --nn) {
+          const float2 dn = d[nn];
+          const float nr = fmaf(pr, sgr, fmaf(-pi, sgi, dn.x));
+          const float ni = fmaf(pr, sgi, fmaf(pi, sgr, dn.y));
+          pr = nr;
+          pi = ni;
+        }
+        for (int q = 0; q < rec_s.n_corner; ++q) {
+          const float wr = rec_s.corner[q][0] + tx, wi = rec_s.corner[q][1] + ty[r];
+          const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
+          const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
+          pr += rec_s.corner[q][2] * pli;
+          pi -= rec_s.corner[q][2] * plr;
+        }
+        const float b1 = rec_s.bx_hi + ((rec_s.bx_lo - ax[r]) + (g.lam_s1 * tx + pr));
+        const float b2 = rec_s.by_hi + ((rec_s.by_lo - ay[r]) + (g.lam_s2 * ty[r] - pi));
+        uint32_t key;
+        const bool ok = pixel_fast(b1, b2, g.inv_sx, g.inv_sy, lo1, hi1, lo2, hi2, rec_s.ix,
+                                   rec_s.iy, g.npix_x, key) && inside;
+        if (MODE == IP_MAP) {
+          bin_warp(a.counts, ok, key);
+        } else if (col == want_i && row == want_j) {
+          a.beta_out[2 * work] = (g.src_x0 + (double)rec_s.ix * g.sx) + (double)b1;
+          a.beta_out[2 * work + 1] = (g.src_y0 + (double)rec_s.iy * g.sy) + (double)b2;
+          if (a.pix_out) a.pix_out[work] = ok ? (int64_t)key : -1;
         }
       }
     }
