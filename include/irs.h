@@ -171,6 +171,26 @@ irs_status irs_shoot_rays(irs_plan_t* plan, const double* lens_xy, const double*
                           const int64_t* ray_idx, int64_t n_idx, double* beta, int64_t* pixel,
                           void* stream);
 
+/* Allocation-free brute-force map.  The paper has no counterpart: this serves
+ * callers that cannot allocate device memory -- code running while another
+ * memory manager owns the device (a caching allocator or a fixed pool),
+ * plug-ins that must not trigger cudaMalloc/cudaFree's implicit device-wide
+ * synchronisation, and latency-critical loops.  It computes what
+ * irs_make_map does for a plan made from `params` with method IRS_BRUTE
+ * (counts overwritten, mag written when not NULL), but takes the parameters
+ * directly and calls no cudaMalloc, cudaFree or other allocating routine: its
+ * scratch is a 7.9 MB file-scope device array that every GPU loading the
+ * library holds until exit.  Limit: the ray lattice must fit 49,152 tiles of
+ * 32 x 64 rays (about 1.0e8 rays); larger lattices return IRS_ERR_OVERFLOW
+ * before any work is enqueued.  The first call on each device looks up the
+ * array's device address (make it before any stream capture).  All calls share
+ * the array: calls whose work overlaps on the GPU race.  Errors: IRS_ERR_ARG,
+ * IRS_ERR_DEGENERATE, IRS_ERR_OVERFLOW, IRS_ERR_UNSUPPORTED (method other than
+ * IRS_BRUTE), IRS_ERR_CUDA. */
+irs_status irs_make_map_brute_noalloc(const irs_params* params, const double* lens_xy,
+                                      const double* mass, int64_t n, uint32_t* counts,
+                                      float* mag, void* stream);
+
 /* Wait for `stream` and return the first error a kernel of this plan raised
  * since the last sync (IRS_OK if none), clearing it. */
 irs_status irs_plan_sync(irs_plan_t* plan, void* stream);

@@ -80,13 +80,15 @@ def _L():
         lib.irs_magnify.argtypes = [vp, vp, vp, vp]
         lib.irs_plan_set_timing.argtypes = [vp, C.c_int32]
         lib.irs_plan_timings.argtypes = [vp, C.POINTER(IrsTimings)]
+        lib.irs_make_map_brute_noalloc.argtypes = [C.POINTER(IrsParams), dp, dp, i64, vp, vp, vp]
         lib.irs_plan_sync.argtypes = [vp, vp]
         lib.irs_plan_destroy.argtypes = [vp]
         lib.irs_status_str.argtypes = [C.c_int]
         lib.irs_status_str.restype = C.c_char_p
         for name in ("irs_plan", "irs_plan_info_get", "irs_make_map", "irs_make_maps_batched",
                      "irs_shoot_rays", "irs_plan_sync", "irs_plan_destroy", "irs_make_map_rows",
-                     "irs_magnify", "irs_plan_set_timing", "irs_plan_timings"):
+                     "irs_magnify", "irs_plan_set_timing", "irs_plan_timings",
+                     "irs_make_map_brute_noalloc"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
     return _lib
@@ -211,6 +213,17 @@ def irs_shoot_rays(plan, lens_xy, mass, ray_idx, beta, pixel=None, stream=None):
                                _ptr(ray_idx, torch.int64, "ray_idx"), int(ray_idx.numel()),
                                _ptr(beta, torch.float64, "beta"), _ptr(pixel, torch.int64, "pixel"),
                                _stream(stream)), "irs_shoot_rays")
+
+
+def irs_make_map_brute_noalloc(params, lens_xy, mass, counts, mag=None, stream=None):
+    """Brute-force map without any device allocation (see include/irs.h): the
+    parameters go in directly, scratch is the library's static device array."""
+    import torch
+    n = int(mass.numel())
+    _check(_L().irs_make_map_brute_noalloc(
+        C.byref(params), _ptr(lens_xy, torch.float64, "lens_xy") if n else None,
+        _ptr(mass, torch.float64, "mass") if n else None, n, _ptr(counts, torch.uint32, "counts"),
+        _ptr(mag, torch.float32, "mag"), _stream(stream)), "irs_make_map_brute_noalloc")
 
 
 def irs_plan_sync(plan, stream=None):
