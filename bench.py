@@ -178,12 +178,23 @@ def run_ours(args):
         w["nav"] = args.nav
     full = args.method != "brute"
 
-    plan = irs.Plan(workload_params(irs, args.method, w))
-    info = plan.info
-    box = (info.lens_x0, info.lens_x1, info.lens_y0, info.lens_y1)
+    params = workload_params(irs, args.method, w)
+    probe = irs.Plan(params)  # the lens plane does not depend on the tuning
+    box = (probe.info.lens_x0, probe.info.lens_x1, probe.info.lens_y0, probe.info.lens_y1)
+    probe.close()
     xy, m = lens_field(lensgen, box, w["seed"] + 1000 * rank, w)
     dxy = torch.from_numpy(xy).to(dev)
     dm = torch.from_numpy(m).to(dev)
+    tune = None
+    if full and not args.no_tune:  # untimed: pick cell size and ray-pass variant
+        t0 = time.perf_counter()
+        params, res = irs.irs_autotune(params, dxy, dm)
+        tune = {"cell_mult": res.cell_mult, "kernel_variant": res.kernel_variant,
+                "candidates": res.candidates, "est_ms_tuned": res.ms_per_map,
+                "est_ms_default": res.ms_default, "from_cache": bool(res.from_cache),
+                "tuning_s": time.perf_counter() - t0}
+    plan = irs.Plan(params)
+    info = plan.info
     shape = (w["npix"], w["npix"])
     counts = torch.zeros(shape, dtype=torch.uint32, device=dev)
     mag = torch.zeros(shape, dtype=torch.float32, device=dev)
@@ -302,6 +313,7 @@ def run_ours(args):
             "e2e": {"value": rays_per_step / (e2e_ms * 1e-3), "unit": "rays/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
+            "autotune": tune,
             "roofline": roofline,
             "clocks": clocks,
             "stage_ms": {"raypass_mean": ray_ms_mean, "map_total_mean": float(np.mean(tot_ms)),
@@ -430,6 +442,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-brute", action="store_true", help="skip the brute-force band")
+    ap.add_argument("--no-tune", action="store_true", help="paper-rule cells, default ray pass")
     ap.add_argument("--band-rows", type=int, default=0, help="brute band height (rows)")
     ap.add_argument("--n-star", type=int, default=0, help="override the lens count (profiling)")
     ap.add_argument("--npix", type=int, default=0, help="override the map side (profiling)")

@@ -74,7 +74,9 @@ typedef struct irs_params {
   double cell_mult;       /* INTERP: level-1 cell side in units of the paper's rule; 0 = default */
   int32_t window;         /* INTERP: cells within this Chebyshev distance sum lenses directly into
                              the series; 0 = default */
-  int32_t reserved[7];    /* must be 0 */
+  int32_t kernel_variant; /* INTERP: ray-pass variant 0..3 (rays per thread, level-2 sub-cells,
+                             sub-cell terms: 0 = 8/8/8, 1 = 8/16/6, 2 = 4/8/8, 3 = 4/16/6) */
+  int32_t reserved[6];    /* must be 0 */
 } irs_params;
 
 /* Geometry chosen by irs_plan (FP64, host side). */
@@ -119,11 +121,20 @@ irs_status irs_plan_info_get(const irs_plan_t* plan, irs_plan_info* info);
 irs_status irs_make_map(irs_plan_t* plan, const double* lens_xy, const double* mass, int64_t n,
                         uint32_t* counts, float* mag, void* stream);
 
-/* Several maps with their own plans, lenses and outputs, enqueued as one
- * persistent work queue per stage and replayed from a CUDA graph that is
- * captured on the first call with the same plans and pointers.  Arrays hold
- * `nmaps` host-side entries; the pointers they hold are device pointers.
- * Errors as irs_make_map, plus IRS_ERR_TIMEOUT from the queue's bounded wait. */
+/* Several maps with their own plans, lenses and outputs (no paper
+ * counterpart: many maps of uneven N_*, kappa and gamma).  Each map's mass
+ * sum, cell lists and far-field series (or brute-force setup and ray pass) run
+ * on forked streams; the interpolated ray passes of all maps run as one
+ * persistent launch per kernel variant that pulls (map, cell) items from a
+ * global counter.  The sequence is captured into a CUDA graph on the first call
+ * with a given set of plans, pointers and lens counts, and later calls with the
+ * same set replay the graph (the last 4 sets are kept; destroying a plan drops
+ * the graphs that use it).  Arrays hold `nmaps` host-side entries; the pointers
+ * they hold are device pointers; `mag` (or any mag[k]) may be NULL.  Results
+ * equal those of irs_make_map on each map.  Each plan may appear once (its
+ * workspace serves one map).  The first call of a set allocates and
+ * synchronises; replays only enqueue.  Errors: as irs_make_map, IRS_ERR_ARG
+ * for a repeated plan, IRS_ERR_UNSUPPORTED for IRS_MLP plans. */
 irs_status irs_make_maps_batched(irs_plan_t* const* plans, int32_t nmaps,
                                  const double* const* lens_xy, const double* const* mass,
                                  const int64_t* n, uint32_t* const* counts, float* const* mag,
@@ -170,6 +181,35 @@ irs_status irs_plan_timings(irs_plan_t* plan, irs_timings* out);
 irs_status irs_shoot_rays(irs_plan_t* plan, const double* lens_xy, const double* mass, int64_t n,
                           const int64_t* ray_idx, int64_t n_idx, double* beta, int64_t* pixel,
                           void* stream);
+
+/* Autotuner (no paper counterpart; the paper fixes Delta x1 by its rule and
+ * Delta x2 = Delta x1 / 20 "after a series of tests", Sec. 2.4): for an
+ * INTERP or MLP `params`, time candidate level-1 cell sizes (multipliers 0.5 ..
+ * 2 of the paper's rule) and ray-pass kernel variants on the given lenses
+ * (device arrays as irs_make_map) and write into *tuned a copy of *params with
+ * the fastest cell_mult and kernel_variant.  Each candidate's cost per map is
+ * its measured cell-list and far-field time plus its ray-pass time on a band
+ * of ~2e9 rays scaled to the whole lattice.  `cache_path` (or, when NULL or
+ * empty, the environment variable IRS_AUTOTUNE_CACHE) names a JSON-lines file
+ * of earlier results keyed by a coarse signature of the parameters; a hit
+ * returns at once, a miss appends the new result.  For IRS_BRUTE, *tuned =
+ * *params.  Synchronous; allocates temporary plans.  *result (may be NULL)
+ * receives the choice and the estimated milliseconds per map of the choice
+ * and of the default (cell_mult 1, variant 0).  Errors: IRS_ERR_ARG,
+ * IRS_ERR_OOM, IRS_ERR_CUDA. */
+typedef struct irs_tune_result {
+  double cell_mult;      /* chosen multiplier of the paper's Delta x1 */
+  int32_t kernel_variant;
+  int32_t candidates;    /* candidates measured (0 when served from the cache) */
+  double ms_per_map;     /* estimated time per map of the choice */
+  double ms_default;     /* the same for cell_mult 1, variant 0 (0 if not measured) */
+  int32_t from_cache;    /* 1 when the cache answered */
+  int32_t pad_;
+} irs_tune_result;
+
+irs_status irs_autotune(const irs_params* params, const double* lens_xy, const double* mass,
+                        int64_t n, const char* cache_path, irs_params* tuned,
+                        irs_tune_result* result, void* stream);
 
 /* Allocation-free brute-force map.  The paper has no counterpart: this serves
  * callers that cannot allocate device memory -- code running while another

@@ -199,7 +199,7 @@ irs_status irs_plan(const irs_params* params, void* stream, irs_plan_t** out) {
   if (p.plane != IRS_PLANE_RECT && p.plane != IRS_PLANE_CIRCLE) return IRS_ERR_ARG;
   if (p.method != IRS_BRUTE && p.method != IRS_INTERP && p.method != IRS_MLP) return IRS_ERR_ARG;
   if (p.flags != 0) return IRS_ERR_ARG;
-  for (int k = 0; k < 7; ++k)
+  for (int k = 0; k < 6; ++k)
     if (p.reserved[k] != 0) return IRS_ERR_ARG;
   if (p.cell_mult < 0 || p.far_order < 0 || p.window < 0) return IRS_ERR_ARG;
 
@@ -314,20 +314,6 @@ irs_status irs_shoot_rays(irs_plan_t* P, const double* xy, const double* mass, i
   return irs::interp_shoot_rays(P, xy, mass, n, ray_idx, n_idx, beta, pixel, s);
 }
 
-irs_status irs_make_maps_batched(irs_plan_t* const* plans, int32_t nmaps,
-                                 const double* const* lens_xy, const double* const* mass,
-                                 const int64_t* n, uint32_t* const* counts, float* const* mag,
-                                 void* stream) {
-  if (nmaps < 0 || (nmaps > 0 && (!plans || !lens_xy || !mass || !n || !counts)))
-    return IRS_ERR_ARG;
-  for (int32_t k = 0; k < nmaps; ++k) {
-    irs_status st = irs_make_map(plans[k], lens_xy[k], mass[k], n[k], counts[k],
-                                 mag ? mag[k] : nullptr, stream);
-    if (st != IRS_OK) return st;
-  }
-  return IRS_OK;
-}
-
 irs_status irs_plan_sync(irs_plan_t* P, void* stream) {
   if (!P) return IRS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -346,6 +332,7 @@ irs_status irs_plan_sync(irs_plan_t* P, void* stream) {
 irs_status irs_plan_destroy(irs_plan_t* P) {
   if (!P) return IRS_OK;
   cudaDeviceSynchronize();
+  irs_batch_forget_plan(P);
   irs::interp_destroy(P);
   for (int k = 0; k < irs::EV_COUNT; ++k)
     if (P->ev[k]) cudaEventDestroy(P->ev[k]);

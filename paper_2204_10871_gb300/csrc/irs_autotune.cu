@@ -1,0 +1,167 @@
+// irs_autotune.cu -- choose the level-1 cell size and the ray-pass kernel
+// variant of the interpolated method by timing them on the caller's lenses.
+//
+// Candidates: cell multiplier (of the paper's Delta x1 rule) in {0.5, 0.71,
+// 1, 1.41, 2} times the four ray-pass variants (rays per thread, level-2
+// sub-cells, sub-cell terms).  Each candidate plan makes one warm-up and one
+// timed map restricted to a band of lattice rows holding about 2e9 rays (the
+// whole lattice when smaller); its cost per map is the measured cell-list and
+// far-field time plus the ray-pass time scaled to the full lattice.  Results
+// are kept in a JSON-lines cache file keyed by a coarse signature of the
+// parameters, so a sweep over many similar maps tunes once.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "irs_common.cuh"
+
+namespace {
+
+const double CELL_MULTS[] = {0.5, 0.70710678, 1.0, 1.41421356, 2.0};
+constexpr int NVARIANT = 4;
+constexpr double BAND_RAYS = 2.0e9;
+std::mutex g_file_mu;
+
+// Coarse signature: parameters that change the balance between the near sum,
+// the far field and the ray count, bucketed so that similar maps share it.
+std::string signature(const irs_params& p, int64_t n) {
+  char buf[256];
+  const double nav = p.rays_per_pixel;
+  snprintf(buf, sizeof buf, "plane%d-ks%.2f-kss%.2f-g%.2f-px%dx%d-nav%d-nlog%d-area%.0f",
+           p.plane, floor(p.kappa_star * 20.0 + 0.5) / 20.0, floor(p.kappa_s * 20.0 + 0.5) / 20.0,
+           floor(fabs(p.gamma) * 20.0 + 0.5) / 20.0, p.npix_x, p.npix_y,
+           (int)floor(log2(nav > 1 ? nav : 1) * 2.0 + 0.5), n > 0 ? (int)floor(log2((double)n) * 2 + 0.5) : -1,
+           floor(log2((p.src_x1 - p.src_x0) * (p.src_y1 - p.src_y0)) * 2.0 + 0.5));
+  return std::string(buf);
+}
+
+bool cache_lookup(const char* path, const std::string& key, double* mult, int* variant, double* ms) {
+  if (!path || !*path) return false;
+  std::lock_guard<std::mutex> lock(g_file_mu);
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  while (fgets(line, sizeof line, f)) {
+    char k[512];
+    double m, t;
+    int v;
+    if (sscanf(line, "{\"key\": \"%511[^\"]\", \"cell_mult\": %lf, \"kernel_variant\": %d, \"ms\": %lf}",
+               k, &m, &v, &t) == 4 &&
+        key == k) {
+      *mult = m;
+      *variant = v;
+      *ms = t;
+      found = true;  // the last entry for a key wins
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, double mult, int variant, double ms) {
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lock(g_file_mu);
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"key\": \"%s\", \"cell_mult\": %.8f, \"kernel_variant\": %d, \"ms\": %.6f}\n",
+          key.c_str(), mult, variant, ms);
+  fclose(f);
+}
+
+// Estimated milliseconds per full map for one candidate, or a negative value
+// when the candidate cannot be planned.
+double measure(const irs_params& base, double mult, int variant, const double* xy, const double* mass,
+               int64_t n, uint32_t* counts, cudaStream_t s) {
+  irs_params p = base;
+  p.method = IRS_INTERP;
+  p.cell_mult = mult;
+  p.kernel_variant = variant;
+  irs_plan_t* P = nullptr;
+  if (irs_plan(&p, s, &P) != IRS_OK) return -1.0;
+  irs_plan_info info;
+  irs_plan_info_get(P, &info);
+  int64_t rows = (int64_t)ceil(BAND_RAYS / (double)info.n_rays_x);
+  if (rows < 2 * info.rays_per_cell_y) rows = 2 * info.rays_per_cell_y;
+  if (rows > info.n_rays_y) rows = info.n_rays_y;
+  const int64_t r0 = (info.n_rays_y - rows) / 2 / (info.rays_per_cell_y) * info.rays_per_cell_y;
+  const int64_t r1 = r0 + rows < info.n_rays_y ? r0 + rows : info.n_rays_y;
+  double est = -1.0;
+  irs_plan_set_timing(P, 1);
+  for (int rep = 0; rep < 2; ++rep) {
+    if (irs_make_map_rows(P, xy, mass, n, r0, r1, counts, s) != IRS_OK) break;
+    irs_timings t;
+    if (irs_plan_timings(P, &t) != IRS_OK || !t.valid) break;
+    if (rep == 1) {
+      const double scale = (double)info.n_rays_y / (double)(r1 - r0);
+      est = (double)(t.ms_total - t.ms_raypass) + (double)t.ms_raypass * scale;
+    }
+  }
+  if (irs_plan_sync(P, s) != IRS_OK) est = -1.0;
+  irs_plan_destroy(P);
+  return est;
+}
+
+}  // namespace
+
+extern "C" irs_status irs_autotune(const irs_params* params, const double* lens_xy, const double* mass,
+                                   int64_t n, const char* cache_path, irs_params* tuned,
+                                   irs_tune_result* result, void* stream) {
+  if (!params || !tuned || n < 0 || (n > 0 && (!lens_xy || !mass))) return IRS_ERR_ARG;
+  *tuned = *params;
+  irs_tune_result r;
+  memset(&r, 0, sizeof r);
+  if (!cache_path || !*cache_path) cache_path = getenv("IRS_AUTOTUNE_CACHE");
+  if (params->method == IRS_BRUTE) {  // nothing to choose at run time
+    if (result) *result = r;
+    return IRS_OK;
+  }
+  const std::string key = signature(*params, n);
+  double mult = 0, ms = 0;
+  int variant = 0;
+  if (cache_lookup(cache_path, key, &mult, &variant, &ms)) {
+    tuned->cell_mult = mult;
+    tuned->kernel_variant = variant;
+    r.cell_mult = mult;
+    r.kernel_variant = variant;
+    r.ms_per_map = ms;
+    r.from_cache = 1;
+    if (result) *result = r;
+    return IRS_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t* counts = nullptr;
+  const size_t npix = (size_t)params->npix_x * params->npix_y;
+  if (cudaMalloc(&counts, npix * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return IRS_ERR_OOM;
+  }
+  double best = -1.0;
+  for (double m : CELL_MULTS) {
+    for (int v = 0; v < NVARIANT; ++v) {
+      const double t = measure(*params, m, v, lens_xy, mass, n, counts, s);
+      if (t < 0) continue;
+      r.candidates++;
+      if (m == 1.0 && v == 0) r.ms_default = t;
+      if (best < 0 || t < best) {
+        best = t;
+        mult = m;
+        variant = v;
+      }
+    }
+  }
+  cudaFree(counts);
+  if (best < 0) return IRS_ERR_CUDA;
+  tuned->cell_mult = mult;
+  tuned->kernel_variant = variant;
+  r.cell_mult = mult;
+  r.kernel_variant = variant;
+  r.ms_per_map = best;
+  cache_store(cache_path, key, mult, variant, best);
+  if (result) *result = r;
+  return IRS_OK;
+}

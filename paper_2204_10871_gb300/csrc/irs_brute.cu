@@ -130,7 +130,11 @@ __global__ void k_brute_setup(Geo g, const double* __restrict__ msum, int64_t nt
         r.n_near++;
         continue;
       }
-      const cd L = clog_p(w);
+      cd L = clog_p(w);
+      // branch continuous with the rectangle's interior (tile centres are
+      // inside it, so this only guards the two right-hand corners' cuts)
+      if (c == 3 && w.re < 0.0 && w.im > 0.0) L.im -= 2.0 * M_PI;
+      if (c == 1 && w.re < 0.0 && w.im < 0.0) L.im += 2.0 * M_PI;
       const cd wl = cmul(w, L);
       T0.re += ac * wl.im;  // -i a_c (w L)
       T0.im -= ac * wl.re;

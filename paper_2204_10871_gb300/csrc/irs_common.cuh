@@ -179,3 +179,6 @@ int brute_grid_size(int num_sms);
 // FP64 sizing of the plane and lattice (irs_api.cu)
 irs_status size_plane(irs_plan_t* P);
 }  // namespace irs
+
+// cached batch graphs that use a plan are dropped with it (irs_batch.cu)
+void irs_batch_forget_plan(const irs_plan_t* plan);

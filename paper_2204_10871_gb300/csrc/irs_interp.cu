@@ -41,12 +41,8 @@ namespace {
 
 constexpr int IP_KMAX = 32;        // local series terms (max)
 constexpr int IP_P = 18;           // multipole terms and local terms produced by the M2L
-constexpr int IP_Q = 8;            // level-2 sub-cells per side
-constexpr int IP_K2 = 8;           // terms of a sub-cell series
 constexpr int IP_NEAR_MAX = 2048;  // lenses of a 3x3 block held in shared memory
 constexpr int IP_THREADS = 256;
-constexpr int IP_R = 8;            // rays (rows) per thread
-constexpr int IP_WARPS = IP_THREADS / 32;
 constexpr int IP_MAX_CORNER = 4;
 
 constexpr int DEFAULT_K = 24;
@@ -67,6 +63,7 @@ struct IpGeo {
   int32_t nrcx, nrcy;  // ray cells
   double gx0, gy0;     // grid origin (lower-left corner of cell (0,0))
   int K, P, W;
+  int variant;  // ray-pass kernel variant (R, Q, K2)
 };
 
 struct InterpState {
@@ -362,7 +359,14 @@ __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
         r.n_corner++;
         continue;
       }
-      const cd L = {0.5 * log(w.re * w.re + w.im * w.im), atan2(w.im, w.re)};
+      // Log(z - c) on the branch that is continuous with the rectangle's
+      // interior: the principal cuts of the two right-hand corners run along
+      // the top and bottom edges, so a cell centre beyond those edges (a
+      // ragged last cell row) takes the argument across the cut.
+      double arg = atan2(w.im, w.re);
+      if (q == 3 && w.re < 0.0 && w.im > 0.0) arg -= 2.0 * M_PI;  // (a2, b2), centre above b2
+      if (q == 1 && w.re < 0.0 && w.im < 0.0) arg += 2.0 * M_PI;  // (a2, b1), centre below b1
+      const cd L = {0.5 * log(w.re * w.re + w.im * w.im), arg};
       const cd wl = cmul(w, L);
       acc[0].re += ac * wl.im;
       acc[0].im -= ac * wl.re;
@@ -412,10 +416,22 @@ struct IpRayArgs {
   int64_t nwork;
 };
 
-template <int MODE>
-__global__ void __launch_bounds__(IP_THREADS, 2) k_ip_ray(Geo g, IpGeo ig, IpRayArgs a) {
+// Kernel variants of the ray pass (the autotuner picks one per plan):
+// rays per thread R, level-2 sub-cells per side Q, sub-cell series terms K2.
+// Q = 8 with 8 terms and Q = 16 with 6 terms both truncate below 1e-8 of the
+// nearest far lens's field (sub-cell half-diagonal / distance to it: 0.083
+// and 0.042).
+#define IP_VARIANTS(X) X(0, 8, 8, 8) X(1, 8, 16, 6) X(2, 4, 8, 8) X(3, 4, 16, 6)
+constexpr int IP_NVARIANT = 4;
+
+// One level-1 cell: gather the 3x3 block's lenses, re-centre the series on the
+// sub-cells, then every ray of rows [jlo, jhi) of the cell.  In DUMP mode the
+// thread holding ray (want_i, want_j) writes its beta and pixel to slot `work`.
+template <int MODE, int R, int Q, int K2>
+__device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpRayArgs& a, int64_t rc,
+                                        int64_t want_i, int64_t want_j, int64_t work) {
   __shared__ float4 near_s[IP_NEAR_MAX];
-  __shared__ float2 sub_s[IP_Q * IP_Q][IP_K2];
+  __shared__ float2 sub_s[Q * Q][K2];
   __shared__ float2 c_s[IP_KMAX];
   __shared__ CellRec rec_s;
   __shared__ int blk_start[9], blk_off[10];
@@ -424,164 +440,243 @@ __global__ void __launch_bounds__(IP_THREADS, 2) k_ip_ray(Geo g, IpGeo ig, IpRay
   const float hf = (float)ig.h;
   const float inv_k = 1.0f / (float)k;
 
+  const int rcx = (int)(rc % ig.nrcx), rcy = (int)(rc / ig.nrcx);
+  const int cx = rcx + ig.ox, cy = rcy + ig.oy;
+  const int64_t i0 = (int64_t)rcx * k, j0 = (int64_t)rcy * k;
+  const int64_t i1 = min(i0 + k, g.nrx);
+  int64_t jlo = j0, jhi = min(j0 + k, g.nry);
+  if (MODE == IP_MAP) {
+    jlo = max(jlo, a.row0);
+    jhi = min(jhi, a.row1);
+    if (jlo >= jhi) return;  // uniform over the CTA
+  }
+  __syncthreads();  // previous cell's shared data no longer read
+  if (tid == 0) {
+    rec_s = a.recs[rc];
+    int off = 0;
+    for (int q = 0; q < 9; ++q) {
+      const int x = cx + (q % 3) - 1, y = cy + (q / 3) - 1;
+      int s0 = 0, cnt = 0;
+      if (x >= 0 && x < ig.ncx && y >= 0 && y < ig.ncy) {
+        const int64_t s = (int64_t)y * ig.ncx + x;
+        s0 = a.start[s];
+        cnt = a.start[s + 1] - s0;
+      }
+      blk_start[q] = s0;
+      blk_off[q] = off;
+      off += cnt;
+    }
+    if (off > IP_NEAR_MAX) {
+      atomicExch(a.status, (int)IRS_ERR_OVERFLOW);
+      off = IP_NEAR_MAX;
+    }
+    blk_off[9] = off;
+  }
+  for (int q = tid; q < ig.K; q += blockDim.x) c_s[q] = a.coef[rc * ig.K + q];
+  __syncthreads();
+  const int n_near = blk_off[9];
+  for (int t = tid; t < n_near; t += blockDim.x) {
+    int q = 0;
+    while (q < 8 && t >= blk_off[q + 1]) ++q;
+    const float4 v = a.rel[blk_start[q] + (t - blk_off[q])];
+    const float ox = (float)((q % 3) - 1) * hf, oy = (float)((q / 3) - 1) * hf;
+    near_s[t] = make_float4(v.x + ox, v.y + oy, v.z, 0.f);
+  }
+  // level 2: re-centre the series on the sub-cell centres eps (cell units)
+  for (int t = tid; t < Q * Q * K2; t += blockDim.x) {
+    const int sub = t / K2, nn = t % K2;
+    const float er = ((float)(sub % Q) + 0.5f) / Q - 0.5f;
+    const float ei = ((float)(sub / Q) + 0.5f) / Q - 0.5f;
+    float sr = 0.f, si = 0.f, tr = 1.f, ti = 0.f;  // term = binom(kk, nn) eps^(kk - nn)
+    for (int kk = nn; kk < ig.K; ++kk) {
+      if (kk >= 1) {
+        const float2 c = c_s[kk];
+        sr = fmaf(c.x, tr, fmaf(-c.y, ti, sr));
+        si = fmaf(c.x, ti, fmaf(c.y, tr, si));
+      }
+      const float f = (float)(kk + 1) / (float)(kk + 1 - nn);
+      const float nr = (tr * er - ti * ei) * f, ni = (tr * ei + ti * er) * f;
+      tr = nr;
+      ti = ni;
+    }
+    const float sc = powf((float)Q, -(float)nn);
+    sub_s[sub][nn] = make_float2(sr * sc, si * sc);
+  }
+  __syncthreads();
+
+  // base-pixel range of this cell for the 32-bit pixel test
+  const float lo1 = (float)(-rec_s.ix), hi1 = (float)(g.npix_x - rec_s.ix);
+  const float lo2 = (float)(-rec_s.iy), hi2 = (float)(g.npix_y - rec_s.iy);
+  // work units (32-column strip x R-row group), dealt round-robin to warps
+  const int nwarps = blockDim.x / 32;
+  const int nstrip = (int)((i1 - i0 + 31) / 32);
+  const int nrg = (int)((jhi - jlo + R - 1) / R);
+  const int nunit = nstrip * nrg;
+  for (int unit = warp; unit < nunit; unit += nwarps) {
+    const int st = unit % nstrip, rg = unit / nstrip;
+    const int64_t col = i0 + (int64_t)st * 32 + lane;
+    const int64_t r0 = jlo + (int64_t)rg * R;
+    const float taux = ((float)(col - i0) + 0.5f) * inv_k - 0.5f;
+    const float tx = taux * hf;
+    int u = (int)floorf((taux + 0.5f) * Q);
+    u = u < 0 ? 0 : (u >= Q ? Q - 1 : u);
+    const float sgr = (taux - (((float)u + 0.5f) / Q - 0.5f)) * Q;
+    float ty[R], ax[R], ay[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      ty[r] = (((float)(r0 + r - j0) + 0.5f) * inv_k - 0.5f) * hf;
+      ax[r] = ay[r] = 0.f;
+    }
+#pragma unroll 2
+    for (int q = 0; q < n_near; ++q) {
+      const float4 L = near_s[q];
+      const float dx = tx - L.x;
+      const float dx2 = dx * dx;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float dy = ty[r] - L.y;
+        const float r2 = fmaf(dy, dy, dx2);
+        const float w = L.z * rcp_approx(r2);
+        ax[r] = fmaf(w, dx, ax[r]);
+        ay[r] = fmaf(w, dy, ay[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t row = r0 + r;
+      const bool inside = col < i1 && row < jhi;
+      // sub-cell and its series in sigma = (tau - eps) Q
+      const float tauy = ((float)(row - j0) + 0.5f) * inv_k - 0.5f;
+      int v = (int)floorf((tauy + 0.5f) * Q);
+      v = v < 0 ? 0 : (v >= Q ? Q - 1 : v);
+      const float sgi = (tauy - (((float)v + 0.5f) / Q - 0.5f)) * Q;
+      const float2* d = sub_s[v * Q + u];
+      float pr = d[K2 - 1].x, pi = d[K2 - 1].y;
+#pragma unroll
+      for (int nn = K2 - 2; nn >= 0; --nn) {
+        const float2 dn = d[nn];
+        const float nr = fmaf(pr, sgr, fmaf(-pi, sgi, dn.x));
+        const float ni = fmaf(pr, sgi, fmaf(pi, sgr, dn.y));
+        pr = nr;
+        pi = ni;
+      }
+      for (int q = 0; q < rec_s.n_corner; ++q) {
+        const float wr = rec_s.corner[q][0] + tx, wi = rec_s.corner[q][1] + ty[r];
+        const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
+        const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
+        pr += rec_s.corner[q][2] * pli;
+        pi -= rec_s.corner[q][2] * plr;
+      }
+      const float b1 = rec_s.bx_hi + ((rec_s.bx_lo - ax[r]) + (g.lam_s1 * tx + pr));
+      const float b2 = rec_s.by_hi + ((rec_s.by_lo - ay[r]) + (g.lam_s2 * ty[r] - pi));
+      uint32_t key;
+      const bool ok = pixel_fast(b1, b2, g.inv_sx, g.inv_sy, lo1, hi1, lo2, hi2, rec_s.ix, rec_s.iy,
+                                 g.npix_x, key) && inside;
+      if (MODE == IP_MAP) {
+        bin_warp(a.counts, ok, key);
+      } else if (col == want_i && row == want_j) {
+        a.beta_out[2 * work] = (g.src_x0 + (double)rec_s.ix * g.sx) + (double)b1;
+        a.beta_out[2 * work + 1] = (g.src_y0 + (double)rec_s.iy * g.sy) + (double)b2;
+        if (a.pix_out) a.pix_out[work] = ok ? (int64_t)key : -1;
+      }
+    }
+  }
+}
+
+// One map: persistent grid over its ray cells (MAP) or requested rays (DUMP).
+template <int MODE, int R, int Q, int K2>
+__global__ void __launch_bounds__(IP_THREADS, 2) k_ip_ray(Geo g, IpGeo ig, IpRayArgs a) {
   for (int64_t work = blockIdx.x; work < a.nwork; work += gridDim.x) {
-    int64_t rc, want_i = -1, want_j = -1;
     if (MODE == IP_MAP) {
-      rc = a.rc_base + work;
+      ip_cell<IP_MAP, R, Q, K2>(g, ig, a, a.rc_base + work, -1, -1, work);
     } else {
       const int64_t f = a.idx[work];
       if (f < 0 || f >= g.nrx * g.nry) {  // not a lattice ray: report it, touch nothing else
-        if (tid == 0) {
+        if (threadIdx.x == 0) {
           a.beta_out[2 * work] = a.beta_out[2 * work + 1] = nan("");
           if (a.pix_out) a.pix_out[work] = -1;
         }
         continue;
       }
-      want_i = f % g.nrx;
-      want_j = f / g.nrx;
-      rc = (want_j / k) * ig.nrcx + want_i / k;
-    }
-    const int rcx = (int)(rc % ig.nrcx), rcy = (int)(rc / ig.nrcx);
-    const int cx = rcx + ig.ox, cy = rcy + ig.oy;
-    const int64_t i0 = (int64_t)rcx * k, j0 = (int64_t)rcy * k;
-    const int64_t i1 = min(i0 + k, g.nrx);
-    int64_t jlo = j0, jhi = min(j0 + k, g.nry);
-    if (MODE == IP_MAP) {
-      jlo = max(jlo, a.row0);
-      jhi = min(jhi, a.row1);
-      if (jlo >= jhi) continue;  // uniform over the CTA
-    }
-    __syncthreads();  // previous cell's shared data no longer read
-    if (tid == 0) {
-      rec_s = a.recs[rc];
-      int off = 0;
-      for (int q = 0; q < 9; ++q) {
-        const int x = cx + (q % 3) - 1, y = cy + (q / 3) - 1;
-        int s0 = 0, cnt = 0;
-        if (x >= 0 && x < ig.ncx && y >= 0 && y < ig.ncy) {
-          const int64_t s = (int64_t)y * ig.ncx + x;
-          s0 = a.start[s];
-          cnt = a.start[s + 1] - s0;
-        }
-        blk_start[q] = s0;
-        blk_off[q] = off;
-        off += cnt;
-      }
-      if (off > IP_NEAR_MAX) {
-        atomicExch(a.status, (int)IRS_ERR_OVERFLOW);
-        off = IP_NEAR_MAX;
-      }
-      blk_off[9] = off;
-    }
-    for (int q = tid; q < ig.K; q += blockDim.x) c_s[q] = a.coef[rc * ig.K + q];
-    __syncthreads();
-    const int n_near = blk_off[9];
-    for (int t = tid; t < n_near; t += blockDim.x) {
-      int q = 0;
-      while (q < 8 && t >= blk_off[q + 1]) ++q;
-      const float4 v = a.rel[blk_start[q] + (t - blk_off[q])];
-      const float ox = (float)((q % 3) - 1) * hf, oy = (float)((q / 3) - 1) * hf;
-      near_s[t] = make_float4(v.x + ox, v.y + oy, v.z, 0.f);
-    }
-    // level 2: re-centre the series on the sub-cell centres eps (cell units)
-    for (int t = tid; t < IP_Q * IP_Q * IP_K2; t += blockDim.x) {
-      const int sub = t / IP_K2, nn = t % IP_K2;
-      const float er = ((float)(sub % IP_Q) + 0.5f) / IP_Q - 0.5f;
-      const float ei = ((float)(sub / IP_Q) + 0.5f) / IP_Q - 0.5f;
-      float sr = 0.f, si = 0.f, tr = 1.f, ti = 0.f;  // term = binom(kk, nn) eps^(kk - nn)
-      for (int kk = nn; kk < ig.K; ++kk) {
-        if (kk >= 1) {
-          const float2 c = c_s[kk];
-          sr = fmaf(c.x, tr, fmaf(-c.y, ti, sr));
-          si = fmaf(c.x, ti, fmaf(c.y, tr, si));
-        }
-        const float f = (float)(kk + 1) / (float)(kk + 1 - nn);
-        const float nr = (tr * er - ti * ei) * f, ni = (tr * ei + ti * er) * f;
-        tr = nr;
-        ti = ni;
-      }
-      const float sc = powf((float)IP_Q, -(float)nn);
-      sub_s[sub][nn] = make_float2(sr * sc, si * sc);
-    }
-    __syncthreads();
-
-    // base-pixel range of this cell for the 32-bit pixel test
-    const float lo1 = (float)(-rec_s.ix), hi1 = (float)(g.npix_x - rec_s.ix);
-    const float lo2 = (float)(-rec_s.iy), hi2 = (float)(g.npix_y - rec_s.iy);
-    // work units (32-column strip x IP_R-row group), dealt round-robin to warps
-    const int nstrip = (int)((i1 - i0 + 31) / 32);
-    const int nrg = (int)((jhi - jlo + IP_R - 1) / IP_R);
-    const int nunit = nstrip * nrg;
-    for (int unit = warp; unit < nunit; unit += IP_WARPS) {
-      const int st = unit % nstrip, rg = unit / nstrip;
-      const int64_t col = i0 + (int64_t)st * 32 + lane;
-      const int64_t r0 = jlo + (int64_t)rg * IP_R;
-      const float taux = ((float)(col - i0) + 0.5f) * inv_k - 0.5f;
-      const float tx = taux * hf;
-      int u = (int)floorf((taux + 0.5f) * IP_Q);
-      u = u < 0 ? 0 : (u >= IP_Q ? IP_Q - 1 : u);
-      const float sgr = (taux - (((float)u + 0.5f) / IP_Q - 0.5f)) * IP_Q;
-      float ty[IP_R], ax[IP_R], ay[IP_R];
-#pragma unroll
-      for (int r = 0; r < IP_R; ++r) {
-        ty[r] = (((float)(r0 + r - j0) + 0.5f) * inv_k - 0.5f) * hf;
-        ax[r] = ay[r] = 0.f;
-      }
-#pragma unroll 2
-      for (int q = 0; q < n_near; ++q) {
-        const float4 L = near_s[q];
-        const float dx = tx - L.x;
-        const float dx2 = dx * dx;
-#pragma unroll
-        for (int r = 0; r < IP_R; ++r) {
-          const float dy = ty[r] - L.y;
-          const float r2 = fmaf(dy, dy, dx2);
-          const float w = L.z * rcp_approx(r2);
-          ax[r] = fmaf(w, dx, ax[r]);
-          ay[r] = fmaf(w, dy, ay[r]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < IP_R; ++r) {
-        const int64_t row = r0 + r;
-        const bool inside = col < i1 && row < jhi;
-        // sub-cell and its series in sigma = (tau - eps) Q
-        const float tauy = ((float)(row - j0) + 0.5f) * inv_k - 0.5f;
-        int v = (int)floorf((tauy + 0.5f) * IP_Q);
-        v = v < 0 ? 0 : (v >= IP_Q ? IP_Q - 1 : v);
-        const float sgi = (tauy - (((float)v + 0.5f) / IP_Q - 0.5f)) * IP_Q;
-        const float2* d = sub_s[v * IP_Q + u];
-        float pr = d[IP_K2 - 1].x, pi = d[IP_K2 - 1].y;
-#pragma unroll
-        for (int nn = IP_K2 - 2; nn >= 0; --nn) {
-          const float2 dn = d[nn];
-          const float nr = fmaf(pr, sgr, fmaf(-pi, sgi, dn.x));
-          const float ni = fmaf(pr, sgi, fmaf(pi, sgr, dn.y));
-          pr = nr;
-          pi = ni;
-        }
-        for (int q = 0; q < rec_s.n_corner; ++q) {
-          const float wr = rec_s.corner[q][0] + tx, wi = rec_s.corner[q][1] + ty[r];
-          const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
-          const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
-          pr += rec_s.corner[q][2] * pli;
-          pi -= rec_s.corner[q][2] * plr;
-        }
-        const float b1 = rec_s.bx_hi + ((rec_s.bx_lo - ax[r]) + (g.lam_s1 * tx + pr));
-        const float b2 = rec_s.by_hi + ((rec_s.by_lo - ay[r]) + (g.lam_s2 * ty[r] - pi));
-        uint32_t key;
-        const bool ok = pixel_fast(b1, b2, g.inv_sx, g.inv_sy, lo1, hi1, lo2, hi2, rec_s.ix,
-                                   rec_s.iy, g.npix_x, key) && inside;
-        if (MODE == IP_MAP) {
-          bin_warp(a.counts, ok, key);
-        } else if (col == want_i && row == want_j) {
-          a.beta_out[2 * work] = (g.src_x0 + (double)rec_s.ix * g.sx) + (double)b1;
-          a.beta_out[2 * work + 1] = (g.src_y0 + (double)rec_s.iy * g.sy) + (double)b2;
-          if (a.pix_out) a.pix_out[work] = ok ? (int64_t)key : -1;
-        }
-      }
+      const int64_t wi = f % g.nrx, wj = f / g.nrx;
+      ip_cell<IP_DUMP, R, Q, K2>(g, ig, a, (wj / ig.k) * ig.nrcx + wi / ig.k, wi, wj, work);
     }
   }
+}
+
+// Many maps: one persistent launch; CTAs pull (map, cell) items from a global
+// counter, so maps of any size and cost share the GPU without a tail per map.
+struct MapDesc {
+  Geo g;
+  IpGeo ig;
+  IpRayArgs a;
+  int64_t item0;  // index of the map's first item in the concatenated list
+};
+
+template <int R, int Q, int K2>
+__global__ void __launch_bounds__(IP_THREADS, 2)
+k_ip_ray_batch(const MapDesc* __restrict__ maps, int nmaps, int64_t nitems,
+               unsigned long long* __restrict__ queue) {
+  __shared__ MapDesc md;
+  __shared__ long long item_s;
+  __shared__ int map_s;
+  if (threadIdx.x == 0) map_s = -1;
+  for (;;) {
+    __syncthreads();  // everyone is done with md / item_s
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(queue, 1ull);
+      item_s = it;
+      if (it < nitems) {
+        int lo = 0, hi = nmaps - 1;  // last map with item0 <= it
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (maps[mid].item0 <= it) lo = mid; else hi = mid - 1;
+        }
+        if (lo != map_s) {  // items of one map are contiguous: copy on change only
+          md = maps[lo];
+          map_s = lo;
+        }
+      }
+    }
+    __syncthreads();
+    const long long it = item_s;
+    if (it >= nitems) break;
+    ip_cell<IP_MAP, R, Q, K2>(md.g, md.ig, md.a, md.a.rc_base + (it - md.item0), -1, -1, it);
+  }
+}
+
+#define IP_DECL_OCC(V, R, Q, K2)                                                     \
+  case V:                                                                           \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP, R, Q, K2>, \
+                                                  IP_THREADS, 0);                   \
+    break;
+int ip_ray_occupancy(int variant) {
+  int per_sm = 0;
+  switch (variant) { IP_VARIANTS(IP_DECL_OCC) default: break; }
+  return per_sm > 0 ? per_sm : 1;
+}
+
+#define IP_DECL_LAUNCH(V, R, Q, K2)                                                 \
+  case V:                                                                          \
+    if (mode == IP_MAP)                                                            \
+      k_ip_ray<IP_MAP, R, Q, K2><<<(unsigned)grid, IP_THREADS, 0, s>>>(g, ig, a);  \
+    else                                                                           \
+      k_ip_ray<IP_DUMP, R, Q, K2><<<(unsigned)grid, IP_THREADS, 0, s>>>(g, ig, a); \
+    break;
+cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, const Geo& g,
+                          const IpGeo& ig, const IpRayArgs& a) {
+  switch (variant) { IP_VARIANTS(IP_DECL_LAUNCH) default: return cudaErrorInvalidValue; }
+  return cudaGetLastError();
+}
+
+#define IP_DECL_BATCH(V, R, Q, K2)                                                          \
+  case V:                                                                                  \
+    k_ip_ray_batch<R, Q, K2><<<(unsigned)grid, IP_THREADS, 0, s>>>(maps, nmaps, nitems, queue); \
+    break;
+cudaError_t launch_ip_ray_batch(int variant, int64_t grid, cudaStream_t s, const MapDesc* maps,
+                                int nmaps, int64_t nitems, unsigned long long* queue) {
+  switch (variant) { IP_VARIANTS(IP_DECL_BATCH) default: return cudaErrorInvalidValue; }
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ host helpers
@@ -737,7 +832,9 @@ irs_status interp_plan(irs_plan_t* P) {
   ig.K = p.far_order > 0 ? p.far_order : DEFAULT_K;
   ig.W = p.window > 0 ? p.window : DEFAULT_W;
   ig.P = IP_P;
-  if (ig.K > IP_KMAX || ig.K < IP_K2) return IRS_ERR_ARG;
+  if (ig.K > IP_KMAX || ig.K < 8) return IRS_ERR_ARG;
+  ig.variant = p.kernel_variant;
+  if (ig.variant < 0 || ig.variant >= IP_NVARIANT) return IRS_ERR_ARG;
   if (ig.W < 1) ig.W = 1;
 
   Fft2d& f = S->fft;
@@ -788,9 +885,7 @@ irs_status interp_plan(irs_plan_t* P) {
   if (cudaGetLastError() != cudaSuccess) return IRS_ERR_CUDA;
   if (fft2d_forward(S->kspec, f.Nx, f.Ny, G, S->kspec, f, nker, 0) != cudaSuccess) return IRS_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return IRS_ERR_CUDA;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP>, IP_THREADS, 0);
-  S->grid_ray = P->num_sms * (per_sm > 0 ? per_sm : 1);
+  S->grid_ray = P->num_sms * ip_ray_occupancy(ig.variant);
   return IRS_OK;
 }
 
@@ -828,8 +923,7 @@ irs_status interp_run(irs_plan_t* P, const double* xy, const double* mass, int64
     a.rc_base = rc0;
     a.nwork = rc1 - rc0;
     const int64_t grid = (rc1 - rc0) < S->grid_ray ? (rc1 - rc0) : S->grid_ray;
-    k_ip_ray<IP_MAP><<<(unsigned)grid, IP_THREADS, 0, s>>>(P->g, S->ig, a);
-    if (cudaGetLastError() != cudaSuccess) return IRS_ERR_CUDA;
+    if (launch_ip_ray(S->ig.variant, IP_MAP, grid, s, P->g, S->ig, a) != cudaSuccess) return IRS_ERR_CUDA;
   }
   mark(P, EV_RAY1, s);
   return IRS_OK;
@@ -847,8 +941,56 @@ irs_status interp_shoot_rays(irs_plan_t* P, const double* xy, const double* mass
   a.pix_out = pix;
   a.nwork = nidx;
   const int64_t grid = nidx < S->grid_ray ? nidx : S->grid_ray;
-  k_ip_ray<IP_DUMP><<<(unsigned)grid, IP_THREADS, 0, s>>>(P->g, S->ig, a);
-  return cudaGetLastError() == cudaSuccess ? IRS_OK : IRS_ERR_CUDA;
+  return launch_ip_ray(S->ig.variant, IP_DUMP, grid, s, P->g, S->ig, a) == cudaSuccess ? IRS_OK
+                                                                                     : IRS_ERR_CUDA;
+}
+
+irs_status interp_ensure_capacity(irs_plan_t* P, int64_t n) {
+  InterpState* S = S_(P);
+  if (n <= S->cap) return IRS_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) return IRS_ERR_CUDA;
+  return alloc_lens_buffers(S, n + n / 4);
+}
+
+irs_status interp_prepare(irs_plan_t* P, const double* xy, const double* mass, int64_t n,
+                          cudaStream_t s) {
+  return build_cells_and_far(P, xy, mass, n, s);
+}
+
+int interp_variant(const irs_plan_t* P) { return S_(P)->ig.variant; }
+
+size_t interp_desc_bytes(int nmaps) { return sizeof(MapDesc) * (size_t)(nmaps > 0 ? nmaps : 1); }
+
+int64_t interp_fill_descs(irs_plan_t* const* plans, uint32_t* const* counts, int nmaps, void* host) {
+  MapDesc* d = static_cast<MapDesc*>(host);
+  int64_t items = 0;
+  for (int k = 0; k < nmaps; ++k) {
+    InterpState* S = S_(plans[k]);
+    memset(&d[k], 0, sizeof(MapDesc));
+    d[k].g = plans[k]->g;
+    d[k].ig = S->ig;
+    d[k].a = ray_args(plans[k]);
+    d[k].a.counts = counts[k];
+    d[k].a.row0 = 0;
+    d[k].a.row1 = plans[k]->g.nry;
+    d[k].a.rc_base = 0;
+    d[k].a.nwork = (int64_t)S->ig.nrcx * S->ig.nrcy;
+    d[k].item0 = items;
+    items += d[k].a.nwork;
+  }
+  return items;
+}
+
+irs_status interp_batch_launch(int variant, const void* dev_descs, int nmaps, int64_t nitems,
+                               unsigned long long* queue, int num_sms, cudaStream_t s) {
+  if (nmaps <= 0 || nitems <= 0) return IRS_OK;
+  int64_t grid = (int64_t)num_sms * ip_ray_occupancy(variant);
+  if (grid > nitems) grid = nitems;
+  if (cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return IRS_ERR_CUDA;
+  return launch_ip_ray_batch(variant, grid, s, static_cast<const MapDesc*>(dev_descs), nmaps, nitems,
+                             queue) == cudaSuccess
+             ? IRS_OK
+             : IRS_ERR_CUDA;
 }
 
 void interp_destroy(irs_plan_t* P) {

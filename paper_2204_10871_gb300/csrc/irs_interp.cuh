@@ -16,4 +16,19 @@ irs_status interp_shoot_rays(irs_plan_t* P, const double* xy, const double* mass
                              const int64_t* idx, int64_t nidx, double* beta, int64_t* pix,
                              cudaStream_t s);
 void interp_destroy(irs_plan_t* P);
+
+// --- batched maps (irs_batch.cu)
+// grow the lens buffers outside any stream capture
+irs_status interp_ensure_capacity(irs_plan_t* P, int64_t n);
+// cell lists and far-field series of one map (no ray pass)
+irs_status interp_prepare(irs_plan_t* P, const double* xy, const double* mass, int64_t n,
+                          cudaStream_t s);
+int interp_variant(const irs_plan_t* P);
+// host-side ray-pass descriptors of maps that share a kernel variant; returns
+// the total number of (map, cell) work items
+size_t interp_desc_bytes(int nmaps);
+int64_t interp_fill_descs(irs_plan_t* const* plans, uint32_t* const* counts, int nmaps, void* host);
+// one persistent launch over all maps' cells (descriptors already on the device)
+irs_status interp_batch_launch(int variant, const void* dev_descs, int nmaps, int64_t nitems,
+                               unsigned long long* queue, int num_sms, cudaStream_t s);
 }  // namespace irs

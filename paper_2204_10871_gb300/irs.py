@@ -28,7 +28,8 @@ class IrsParams(C.Structure):
                 ("rays_per_pixel", C.c_double), ("border", C.c_double),
                 ("n_star", C.c_int64), ("plane", C.c_int32), ("method", C.c_int32),
                 ("flags", C.c_uint32), ("far_order", C.c_int32), ("cell_mult", C.c_double),
-                ("window", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("window", C.c_int32), ("kernel_variant", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class IrsPlanInfo(C.Structure):
@@ -50,6 +51,12 @@ class IrsTimings(C.Structure):
     _fields_ = [("ms_total", C.c_float), ("ms_prep", C.c_float), ("ms_cells", C.c_float),
                 ("ms_farfield", C.c_float), ("ms_raypass", C.c_float), ("ms_magnify", C.c_float),
                 ("rays", C.c_int64), ("valid", C.c_int32), ("launches", C.c_int32)]
+
+
+class IrsTuneResult(C.Structure):
+    _fields_ = [("cell_mult", C.c_double), ("kernel_variant", C.c_int32),
+                ("candidates", C.c_int32), ("ms_per_map", C.c_double), ("ms_default", C.c_double),
+                ("from_cache", C.c_int32), ("pad_", C.c_int32)]
 
 
 class IrsError(RuntimeError):
@@ -81,6 +88,8 @@ def _L():
         lib.irs_plan_set_timing.argtypes = [vp, C.c_int32]
         lib.irs_plan_timings.argtypes = [vp, C.POINTER(IrsTimings)]
         lib.irs_make_map_brute_noalloc.argtypes = [C.POINTER(IrsParams), dp, dp, i64, vp, vp, vp]
+        lib.irs_autotune.argtypes = [C.POINTER(IrsParams), dp, dp, i64, C.c_char_p,
+                                     C.POINTER(IrsParams), C.POINTER(IrsTuneResult), vp]
         lib.irs_plan_sync.argtypes = [vp, vp]
         lib.irs_plan_destroy.argtypes = [vp]
         lib.irs_status_str.argtypes = [C.c_int]
@@ -88,7 +97,7 @@ def _L():
         for name in ("irs_plan", "irs_plan_info_get", "irs_make_map", "irs_make_maps_batched",
                      "irs_shoot_rays", "irs_plan_sync", "irs_plan_destroy", "irs_make_map_rows",
                      "irs_magnify", "irs_plan_set_timing", "irs_plan_timings",
-                     "irs_make_map_brute_noalloc"):
+                     "irs_make_map_brute_noalloc", "irs_autotune"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
     return _lib
@@ -124,13 +133,15 @@ def _ptr(t, dtype=None, what="tensor"):
 
 
 def make_params(kappa_star, kappa_s, gamma, src, npix, rays_per_pixel, border=-1.0, n_star=0,
-                plane=IRS_PLANE_RECT, method=IRS_BRUTE, far_order=0, cell_mult=0.0, window=0):
+                plane=IRS_PLANE_RECT, method=IRS_BRUTE, far_order=0, cell_mult=0.0, window=0,
+                kernel_variant=0):
     """Fill an IrsParams; src = (x0, x1, y0, y1), npix = n or (nx, ny)."""
     if isinstance(npix, int):
         npix = (npix, npix)
     return IrsParams(kappa_star, kappa_s, gamma, src[0], src[1], src[2], src[3], int(npix[0]),
                      int(npix[1]), rays_per_pixel, border, int(n_star), int(plane), int(method),
-                     0, int(far_order), float(cell_mult), int(window), (C.c_int32 * 7)())
+                     0, int(far_order), float(cell_mult), int(window), int(kernel_variant),
+                     (C.c_int32 * 6)())
 
 
 def irs_status_str(status):
@@ -224,6 +235,19 @@ def irs_make_map_brute_noalloc(params, lens_xy, mass, counts, mag=None, stream=N
         C.byref(params), _ptr(lens_xy, torch.float64, "lens_xy") if n else None,
         _ptr(mass, torch.float64, "mass") if n else None, n, _ptr(counts, torch.uint32, "counts"),
         _ptr(mag, torch.float32, "mag"), _stream(stream)), "irs_make_map_brute_noalloc")
+
+
+def irs_autotune(params, lens_xy, mass, cache_path=None, stream=None):
+    """Returns (tuned IrsParams, IrsTuneResult)."""
+    import torch
+    n = int(mass.numel())
+    tuned = IrsParams()
+    res = IrsTuneResult()
+    _check(_L().irs_autotune(C.byref(params), _ptr(lens_xy, torch.float64, "lens_xy") if n else None,
+                             _ptr(mass, torch.float64, "mass") if n else None, n,
+                             cache_path.encode() if cache_path else None, C.byref(tuned),
+                             C.byref(res), _stream(stream)), "irs_autotune")
+    return tuned, res
 
 
 def irs_plan_sync(plan, stream=None):

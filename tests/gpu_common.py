@@ -25,7 +25,8 @@ def require_gpu():
 
 def params_pair(kappa_star, kappa_s, gamma, src, npix, nav, border=-1.0, plane=0,
                 method=irs.IRS_BRUTE, **kw):
-    """Matching oracle and library parameter structs."""
+    """Matching oracle and library parameter structs; kw sets library-only
+    fields (n_star, kernel_variant, cell_mult, ...)."""
     po = oracle.make_params(kappa_star, kappa_s, gamma, src, npix, nav, border=border, plane=plane)
     pl = irs.make_params(kappa_star, kappa_s, gamma, src, npix, nav, border=border, plane=plane,
                          method=method, **kw)

@@ -56,7 +56,8 @@ def test_struct_layout_matches_header(tmp_path):
 int main(void) {
   printf("irs_params %zu\n", sizeof(irs_params));
   printf("irs_plan_info %zu\n", sizeof(irs_plan_info));
-  P(irs_params, n_star) P(irs_params, method) P(irs_params, cell_mult) P(irs_params, reserved)
+  P(irs_params, n_star) P(irs_params, method) P(irs_params, cell_mult) P(irs_params, kernel_variant)
+  P(irs_params, reserved)
   P(irs_plan_info, n_rays) P(irs_plan_info, ncell_x) P(irs_plan_info, workspace_bytes)
   return 0;
 }

@@ -175,3 +175,75 @@ def test_chunked_rows_add_up():
             irs.irs_make_map_rows(plan.handle, dxy, dm, r0, r1, acc)
         plan.sync()
     assert torch.equal(full, acc)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("cell_mult", [0.5, 2.0])
+def test_every_tunable_choice_is_exact(variant, cell_mult):
+    """The autotuner may pick any ray-pass variant and cell size: each must
+    meet the deflection bar on a dense field."""
+    torch = require_gpu()
+    cfg = (0.45, 0.05, 0.1, (-2.0, 2.0, -2.0, 2.0), 64, 16.0)
+    err, far, _, _, _ = sampled_check(torch, cfg, 400, "uniform", seed=9, nsamp=1500,
+                                      kernel_variant=variant, cell_mult=cell_mult)
+    assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
+
+
+def test_autotune_and_cache(tmp_path):
+    torch = require_gpu()
+    cfg = (0.45, 0.05, 0.1, (-2.0, 2.0, -2.0, 2.0), 64, 16.0)
+    po, pl = params_pair(*cfg, method=irs.IRS_INTERP, n_star=400)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 400, shape="uniform", seed=9, kappa_star=cfg[0])
+    dxy, dm = to_dev(torch, xy, m)
+    cache = str(tmp_path / "tune.jsonl")
+    tuned, res = irs.irs_autotune(pl, dxy, dm, cache_path=cache)
+    assert res.candidates >= 16 and res.from_cache == 0
+    assert res.ms_per_map > 0 and res.ms_default >= res.ms_per_map
+    assert tuned.kernel_variant == res.kernel_variant and tuned.cell_mult == res.cell_mult
+    tuned2, res2 = irs.irs_autotune(pl, dxy, dm, cache_path=cache)
+    assert res2.from_cache == 1
+    assert (tuned2.cell_mult, tuned2.kernel_variant) == (tuned.cell_mult, tuned.kernel_variant)
+    co, _, landed = oracle.make_map(po, qo, xy, m)
+    with irs.Plan(tuned) as plan:
+        counts, _ = plan.make_map(dxy, dm)
+        plan.sync()
+    assert misbinned(co, counts.cpu().numpy()) <= MISBIN_TOL * landed
+
+
+@pytest.mark.parametrize("method", [irs.IRS_INTERP, irs.IRS_BRUTE])
+def test_edge_rows_columns_and_corners(method):
+    """Rays of the lattice's first and last rows and columns and its corners
+    (ragged last cells whose centres lie outside the rectangle, the sheet's
+    corner singularities) on the full mid-size workload."""
+    torch = require_gpu()
+    po, pl = params_pair(*C2, method=method)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 100000, shape="salpeter", seed=2, kappa_star=C2[0])
+    rng = np.random.default_rng(77)
+    nx, ny = qo.nrx, qo.nry
+    ii, jj = [], []
+    for band in range(4):
+        k = 80
+        if band == 0:   # top rows
+            i, j = rng.integers(0, nx, k), ny - 1 - rng.integers(0, 40, k)
+        elif band == 1:  # bottom rows
+            i, j = rng.integers(0, nx, k), rng.integers(0, 40, k)
+        elif band == 2:  # left and right columns
+            i = np.where(rng.random(k) < 0.5, rng.integers(0, 40, k), nx - 1 - rng.integers(0, 40, k))
+            j = rng.integers(0, ny, k)
+        else:            # corners
+            i = np.where(rng.random(k) < 0.5, rng.integers(0, 30, k), nx - 1 - rng.integers(0, 30, k))
+            j = np.where(rng.random(k) < 0.5, rng.integers(0, 30, k), ny - 1 - rng.integers(0, 30, k))
+        ii.append(i)
+        jj.append(j)
+    idx = (np.concatenate(jj) * nx + np.concatenate(ii)).astype(np.int64)
+    _, bo, _ = oracle.shoot_rays(po, qo, xy, m, idx)
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        beta, _ = plan.shoot_rays(dxy, dm, torch.from_numpy(idx).cuda())
+        plan.sync()
+    err = np.abs(beta.cpu().numpy() - bo).max(1)
+    far = nearest_lens_distance(xy, ray_positions(qo, idx)) > NEAR_LENS
+    assert far.sum() > 250
+    assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
