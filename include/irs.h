@@ -211,6 +211,56 @@ irs_status irs_autotune(const irs_params* params, const double* lens_xy, const d
                         int64_t n, const char* cache_path, irs_params* tuned,
                         irs_tune_result* result, void* stream);
 
+/* ---- Learned far field (no paper counterpart).  An IRS_MLP plan sums, for
+ * each level-1 cell, the lenses within a smooth window of R_f = 8 cells
+ * directly and takes the rest of the far field -- the "far-far" part minus
+ * the sheet's analytic part -- from a coordinate network: Fourier features
+ * [sin, cos](pi B x) of the cell centre (32 frequencies), three tanh layers of
+ * width 64, 8 outputs (4 complex series coefficients).  Cells near the
+ * rectangle's corners keep an exact direct sum.  Until irs_mlp_train has run,
+ * an IRS_MLP plan computes the exact FFT far field of IRS_INTERP (fallback).
+ * The network learns the far field of ONE lens field: make maps with the
+ * lenses it was trained on. */
+typedef struct irs_mlp_report {
+  int64_t samples;       /* training samples (direct sums at random points) */
+  int32_t steps;         /* AdamW steps, batch 4096 */
+  int32_t trained;       /* 1 on success */
+  double loss_first;     /* standardised MSE, mean of the first 20 steps */
+  double loss_final;     /* the same, last 20 steps */
+  double valid_rel_rms;  /* held-out: RMS(prediction - target) / RMS(target), physical units */
+  double target_rms;     /* RMS of the targets (theta_E, per output) */
+  double ms_samples;     /* time to generate the samples (GPU direct sums) */
+  double ms_train;       /* time of the training loop */
+} irs_mlp_report;
+
+/* Train the plan's network on the lens field (device arrays as irs_make_map):
+ * n_samples direct-sum targets at seeded random points of the plane (0:
+ * 1,048,576, the maximum), `steps` AdamW steps (0: 3000) of 4096 samples with
+ * BF16 tensor-core forward/backward kernels, FP32 accumulation and FP32
+ * master weights.  Synchronous.  Errors: IRS_ERR_ARG, IRS_ERR_UNSUPPORTED (not
+ * an IRS_MLP plan), IRS_ERR_OOM, IRS_ERR_CUDA. */
+irs_status irs_mlp_train(irs_plan_t* plan, const double* lens_xy, const double* mass, int64_t n,
+                         int64_t n_samples, int32_t steps, uint64_t seed, irs_mlp_report* report,
+                         void* stream);
+
+/* Copy the network's 13,000 FP32 parameters (packed W1, b1, W2, b2, W3, b3, W4,
+ * b4, row-major W[out][in]) and its 32 x 2 Fourier matrix in (host arrays;
+ * NULL leaves a part unchanged) and/or out.  Synchronous.  Errors:
+ * IRS_ERR_UNSUPPORTED (not an IRS_MLP plan), IRS_ERR_CUDA. */
+irs_status irs_mlp_params(irs_plan_t* plan, const float* theta_in, const float* freq_in,
+                          float* theta_out, float* freq_out);
+
+/* Parity path of the training kernel: the loss sum (device double, sum of
+ * squared errors) and the gradient of the mean squared error (device float
+ * [13000]) over the n inputs x (device float [n][2]) and targets t (device
+ * float [n][8]), computed by the same kernel as one training step. */
+irs_status irs_mlp_grad(irs_plan_t* plan, const float* x, const float* t, int64_t n, float* grad,
+                        double* loss_sum, void* stream);
+
+/* Network outputs y (device float [n][8], standardised units) at inputs x
+ * (device float [n][2]). */
+irs_status irs_mlp_forward(irs_plan_t* plan, const float* x, int64_t n, float* y, void* stream);
+
 /* Allocation-free brute-force map.  The paper has no counterpart: this serves
  * callers that cannot allocate device memory -- code running while another
  * memory manager owns the device (a caching allocator or a fixed pool),

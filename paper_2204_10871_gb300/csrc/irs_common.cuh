@@ -149,6 +149,8 @@ struct irs_plan {
   int num_sms;
   // INTERP state (irs_interp.cu)
   void* interp;
+  // learned far field state (irs_mlp.cu), IRS_MLP plans only
+  void* mlp;
   // stage timing (irs_plan_set_timing)
   int timing;
   cudaEvent_t ev[8];

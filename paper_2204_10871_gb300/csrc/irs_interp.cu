@@ -34,6 +34,7 @@
 
 #include "irs_fft.cuh"
 #include "irs_interp.cuh"
+#include "irs_mlp.cuh"
 
 namespace irs {
 
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, double2* __restr
 // Per ray cell: window P2L, M2L result, sheet series, centre term, base pixel.
 __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
                               const int32_t* __restrict__ start, const double2* __restrict__ pos,
-                              const double* __restrict__ m, const double2* __restrict__ conv,
+                              const double* __restrict__ m, const double2* __restrict__ conv, MlpFar far,
                               CellRec* __restrict__ recs, float2* __restrict__ coef) {
   const int64_t rc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nrc = (int64_t)ig.nrcx * ig.nrcy;
@@ -298,19 +299,26 @@ __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
 
   cd acc[IP_KMAX];  // coefficients of tau^k before the 1/h of the lens parts
   for (int k = 0; k < K; ++k) acc[k] = {0.0, 0.0};
-  // window ring: lenses of cells at Chebyshev distance 2..W, directly
-  for (int dy = -ig.W; dy <= ig.W; ++dy) {
+  // direct ring: lenses of cells at Chebyshev distance 2..W (series mode), or
+  // every lens outside the near block weighted by w(r) out to R_f (network mode)
+  const int Wd = far.active ? (int)ceil(far.rf) + 1 : ig.W;
+  for (int dy = -Wd; dy <= Wd; ++dy) {
     const int y = cy + dy;
     if (y < 0 || y >= ig.ncy) continue;
-    for (int dx = -ig.W; dx <= ig.W; ++dx) {
+    for (int dx = -Wd; dx <= Wd; ++dx) {
       if (abs(dx) <= 1 && abs(dy) <= 1) continue;
       const int x = cx + dx;
       if (x < 0 || x >= ig.ncx) continue;
       const int64_t s = (int64_t)y * ig.ncx + x;
       for (int p = start[s]; p < start[s + 1]; ++p) {
         const cd d = {(pos[p].x - zx) * inv_h, (pos[p].y - zy) * inv_h};
+        double wm = m[p];
+        if (far.active) {
+          wm *= mlp_ring_weight(hypot(d.re, d.im), far.rf);
+          if (wm == 0.0) continue;
+        }
         const cd inv = crecip(d);
-        cd pw = {m[p] * inv.re, m[p] * inv.im};
+        cd pw = {wm * inv.re, wm * inv.im};
         for (int k = 0; k < K; ++k) {  // + m d^-(k+1)
           acc[k].re += pw.re;
           acc[k].im += pw.im;
@@ -319,15 +327,27 @@ __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
       }
     }
   }
-  // outer cells through the FFT convolution
-  for (int k = 0; k < IP_P && k < K; ++k) {
-    const double2 v = conv[(int64_t)k * ncells + c];
-    acc[k].re += v.x;
-    acc[k].im += v.y;
+  // outer cells through the FFT convolution (series mode)
+  if (!far.active) {
+    for (int k = 0; k < IP_P && k < K; ++k) {
+      const double2 v = conv[(int64_t)k * ncells + c];
+      acc[k].re += v.x;
+      acc[k].im += v.y;
+    }
   }
   for (int k = 0; k < K; ++k) {
     acc[k].re *= inv_h;
     acc[k].im *= inv_h;
+  }
+  // network mode away from corners: G = -L_ring - U - kappa_* conj(z_C); the
+  // sheet's g cancels against the definition of U
+  const bool learned = far.active && far.corner[rc] < 0;
+  if (far.active && !learned) {  // corner zone: exact far-far sum, then the sheet as usual
+    const double2* ex = far.exact + (int64_t)far.corner[rc] * MLP_KEXACT;
+    for (int k = 0; k < MLP_KEXACT && k < K; ++k) {
+      acc[k].re -= ex[k].x;
+      acc[k].im -= ex[k].y;
+    }
   }
 
   const double ks = g.kstar_scale * msum[0];
@@ -337,7 +357,17 @@ __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
   r.pad_ = 0;
   for (int q = 0; q < IP_MAX_CORNER; ++q) r.corner[q][0] = r.corner[q][1] = r.corner[q][2] = r.corner[q][3] = 0.f;
   cd B;
-  if (g.plane == IRS_PLANE_CIRCLE) {
+  if (learned) {
+    const double ks0 = g.kstar_scale * msum[0];
+    for (int k = 0; k < MLP_KFF && k < K; ++k) {
+      const float2 u = far.U[rc * MLP_KFF + k];
+      acc[k].re -= (double)u.x;
+      acc[k].im -= (double)u.y;
+    }
+    acc[0].re -= ks0 * zx;  // kappa_* conj(z_C)
+    acc[0].im += ks0 * zy;
+    B = {(1.0 - g.kappa_s - g.gamma) * zx, -(1.0 - g.kappa_s + g.gamma) * zy};
+  } else if (g.plane == IRS_PLANE_CIRCLE) {
     B = {(1.0 - g.kappa_s - g.gamma) * zx - ks * g.cx, -(1.0 - g.kappa_s + g.gamma) * zy + ks * g.cy};
   } else {
     // sheet: g(z) = kappa_* (z - 2 a2) + sum_c -i a_c (z - c) Log(z - c); adds g_k h^k
@@ -727,7 +757,7 @@ void mark(irs_plan_t* P, int slot, cudaStream_t s) {
   } while (0)
 
 // kernel launches of one map, reported through irs_plan_timings
-int far_launches(int64_t n) { return (n > 0 ? 4 : 0) + 3 + 1 + 2 + 1 + 2 + 1; }
+int far_launches(int64_t n) { return (n > 0 ? 4 : 0) + 3 + 1 + 2 + 1 + 2 + 1; }  // series mode
 
 irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* mass, int64_t n,
                                cudaStream_t s) {
@@ -757,17 +787,23 @@ irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* ma
   }
   IP_TRY(cudaGetLastError());
   mark(P, EV_CELLS, s);
-  // far field
-  k_ip_p2m<<<(unsigned)((ncells + 127) / 128), 128, 0, s>>>(ig, S->cell_start, S->lens_pos, S->lens_m, S->mpole);
-  IP_TRY(cudaGetLastError());
-  IP_TRY(fft2d_forward(S->mpole, ig.ncx, ig.ncy, ncells, S->spec, S->fft, ig.P, s));
-  const int64_t G = (int64_t)S->fft.Nx * S->fft.Ny;
-  k_ip_m2l_freq<<<(unsigned)((G + 127) / 128), 128, 0, s>>>(G, S->spec, S->kspec);
-  IP_TRY(cudaGetLastError());
-  IP_TRY(fft2d_inverse(S->spec, S->fft, ig.ncx, ig.ncy, S->conv, ncells, ig.P, s));
+  // far field: the network (trained IRS_MLP plans) or the FFT series
+  MlpFar far{};
+  if (P->p.method == IRS_MLP && mlp_trained(P)) {
+    irs_status st = mlp_prepare(P, xy, mass, n, ig.gx0, ig.gy0, ig.h, ig.nrcx, ig.nrcy, ig.ox, ig.oy, &far, s);
+    if (st != IRS_OK) return st;
+  } else {
+    k_ip_p2m<<<(unsigned)((ncells + 127) / 128), 128, 0, s>>>(ig, S->cell_start, S->lens_pos, S->lens_m, S->mpole);
+    IP_TRY(cudaGetLastError());
+    IP_TRY(fft2d_forward(S->mpole, ig.ncx, ig.ncy, ncells, S->spec, S->fft, ig.P, s));
+    const int64_t G = (int64_t)S->fft.Nx * S->fft.Ny;
+    k_ip_m2l_freq<<<(unsigned)((G + 127) / 128), 128, 0, s>>>(G, S->spec, S->kspec);
+    IP_TRY(cudaGetLastError());
+    IP_TRY(fft2d_inverse(S->spec, S->fft, ig.ncx, ig.ncy, S->conv, ncells, ig.P, s));
+  }
   const int64_t nrc = (int64_t)ig.nrcx * ig.nrcy;
   k_ip_finalize<<<(unsigned)((nrc + 63) / 64), 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start, S->lens_pos,
-                                                          S->lens_m, S->conv, S->recs, S->coef);
+                                                          S->lens_m, S->conv, far, S->recs, S->coef);
   IP_TRY(cudaGetLastError());
   mark(P, EV_FAR, s);
   return IRS_OK;
@@ -886,8 +922,15 @@ irs_status interp_plan(irs_plan_t* P) {
   if (fft2d_forward(S->kspec, f.Nx, f.Ny, G, S->kspec, f, nker, 0) != cudaSuccess) return IRS_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return IRS_ERR_CUDA;
   S->grid_ray = P->num_sms * ip_ray_occupancy(ig.variant);
+  if (p.method == IRS_MLP) {
+    if (p.plane != IRS_PLANE_RECT) return IRS_ERR_UNSUPPORTED;
+    irs_status st2 = mlp_plan(P, ig.gx0, ig.gy0, ig.h, ig.ncx, ig.ncy, ig.nrcx, ig.nrcy, ig.ox, ig.oy, 1 << 20);
+    if (st2 != IRS_OK) return st2;
+  }
   return IRS_OK;
 }
+
+double interp_cell_side(const irs_plan_t* P) { return S_(P) ? S_(P)->ig.h : 0.0; }
 
 void interp_fill_info(const irs_plan_t* P, irs_plan_info* info) {
   const InterpState* S = S_(P);
@@ -994,6 +1037,7 @@ irs_status interp_batch_launch(int variant, const void* dev_descs, int nmaps, in
 }
 
 void interp_destroy(irs_plan_t* P) {
+  mlp_destroy(P);
   InterpState* S = S_(P);
   if (!S) return;
   if (S->ws) cudaFree(S->ws);

@@ -59,6 +59,13 @@ class IrsTuneResult(C.Structure):
                 ("from_cache", C.c_int32), ("pad_", C.c_int32)]
 
 
+class IrsMlpReport(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("steps", C.c_int32), ("trained", C.c_int32),
+                ("loss_first", C.c_double), ("loss_final", C.c_double),
+                ("valid_rel_rms", C.c_double), ("target_rms", C.c_double),
+                ("ms_samples", C.c_double), ("ms_train", C.c_double)]
+
+
 class IrsError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -90,6 +97,12 @@ def _L():
         lib.irs_make_map_brute_noalloc.argtypes = [C.POINTER(IrsParams), dp, dp, i64, vp, vp, vp]
         lib.irs_autotune.argtypes = [C.POINTER(IrsParams), dp, dp, i64, C.c_char_p,
                                      C.POINTER(IrsParams), C.POINTER(IrsTuneResult), vp]
+        lib.irs_mlp_train.argtypes = [vp, dp, dp, i64, i64, C.c_int32, C.c_uint64,
+                                      C.POINTER(IrsMlpReport), vp]
+        fp = C.POINTER(C.c_float)
+        lib.irs_mlp_params.argtypes = [vp, fp, fp, fp, fp]
+        lib.irs_mlp_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        lib.irs_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
         lib.irs_plan_sync.argtypes = [vp, vp]
         lib.irs_plan_destroy.argtypes = [vp]
         lib.irs_status_str.argtypes = [C.c_int]
@@ -97,7 +110,8 @@ def _L():
         for name in ("irs_plan", "irs_plan_info_get", "irs_make_map", "irs_make_maps_batched",
                      "irs_shoot_rays", "irs_plan_sync", "irs_plan_destroy", "irs_make_map_rows",
                      "irs_magnify", "irs_plan_set_timing", "irs_plan_timings",
-                     "irs_make_map_brute_noalloc", "irs_autotune"):
+                     "irs_make_map_brute_noalloc", "irs_autotune", "irs_mlp_train",
+                     "irs_mlp_params", "irs_mlp_grad", "irs_mlp_forward"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
     return _lib
@@ -248,6 +262,48 @@ def irs_autotune(params, lens_xy, mass, cache_path=None, stream=None):
                              cache_path.encode() if cache_path else None, C.byref(tuned),
                              C.byref(res), _stream(stream)), "irs_autotune")
     return tuned, res
+
+
+def irs_mlp_train(plan, lens_xy, mass, n_samples=0, steps=0, seed=1, stream=None):
+    import torch
+    n = int(mass.numel())
+    rep = IrsMlpReport()
+    _check(_L().irs_mlp_train(C.c_void_p(plan), _ptr(lens_xy, torch.float64, "lens_xy") if n else None,
+                              _ptr(mass, torch.float64, "mass") if n else None, n, int(n_samples),
+                              int(steps), int(seed), C.byref(rep), _stream(stream)), "irs_mlp_train")
+    return rep
+
+
+def irs_mlp_params(plan, theta_in=None, freq_in=None):
+    """Set (numpy float32 arrays, optional) and return (theta, freq) as numpy arrays."""
+    import numpy as np
+    fp = C.POINTER(C.c_float)
+    tin = None if theta_in is None else np.ascontiguousarray(theta_in, dtype=np.float32)
+    fin = None if freq_in is None else np.ascontiguousarray(freq_in, dtype=np.float32)
+    tout = np.zeros(13000, dtype=np.float32)
+    fout = np.zeros(64, dtype=np.float32)
+    _check(_L().irs_mlp_params(C.c_void_p(plan), None if tin is None else tin.ctypes.data_as(fp),
+                               None if fin is None else fin.ctypes.data_as(fp),
+                               tout.ctypes.data_as(fp), fout.ctypes.data_as(fp)), "irs_mlp_params")
+    return tout, fout.reshape(32, 2)
+
+
+def irs_mlp_grad(plan, x, t, stream=None):
+    """x: (n, 2) float32 CUDA, t: (n, 8) float32 CUDA -> (grad (13000,) float32, loss_sum) on CUDA."""
+    import torch
+    grad = torch.empty(13000, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float64, device=x.device)
+    _check(_L().irs_mlp_grad(C.c_void_p(plan), _ptr(x, torch.float32, "x"), _ptr(t, torch.float32, "t"),
+                             int(x.shape[0]), _ptr(grad), _ptr(loss), _stream(stream)), "irs_mlp_grad")
+    return grad, loss
+
+
+def irs_mlp_forward(plan, x, stream=None):
+    import torch
+    y = torch.empty((x.shape[0], 8), dtype=torch.float32, device=x.device)
+    _check(_L().irs_mlp_forward(C.c_void_p(plan), _ptr(x, torch.float32, "x"), int(x.shape[0]), _ptr(y),
+                                _stream(stream)), "irs_mlp_forward")
+    return y
 
 
 def irs_plan_sync(plan, stream=None):
