@@ -38,6 +38,11 @@ WORKLOAD = dict(name="paper-mid: kappa*=0.45 kappa_s=0 gamma=0.45, 1e5 Salpeter 
                      "2000^2 px over 20x20 thetaE, 100 rays/px",
                 kappa_star=0.45, kappa_s=0.0, gamma=0.45, S=20.0, npix=2000, nav=100.0,
                 n_star=100000, shape="salpeter", seed=2)
+# the learned far field's workload
+WORKLOAD_LEARNED = dict(name="learned: kappa*=0.4 kappa_s=0.1 gamma=0.35, 2e5 equal-mass lenses, "
+                             "4000^2 px over 20x20 thetaE, 64 rays/px",
+                        kappa_star=0.4, kappa_s=0.1, gamma=0.35, S=20.0, npix=4000, nav=64.0,
+                        n_star=200000, shape="equal", seed=5)
 BRUTE_ROWS = 256            # band of lattice rows for the brute-force timing
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
@@ -105,6 +110,19 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+def slowest_rank_ms(my_ms, dist, device):
+    """Max over ranks of this rank's timed milliseconds (the job ends with the slowest)."""
+    import torch
+    t = torch.tensor([float(my_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rays_per_s(rays_per_step_per_rank, world, ms_per_step):
+    """Weak scaling: every rank makes its own map, so the job shoots world x the rays."""
+    return rays_per_step_per_rank * world / (ms_per_step * 1e-3)
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -169,7 +187,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(local)
     n_sms = props.multi_processor_count
-    w = dict(WORKLOAD)
+    w = dict(WORKLOAD_LEARNED if args.method == "mlp" else WORKLOAD)
     if args.n_star:
         w["n_star"] = args.n_star
     if args.npix:
@@ -186,7 +204,7 @@ def run_ours(args):
     dxy = torch.from_numpy(xy).to(dev)
     dm = torch.from_numpy(m).to(dev)
     tune = None
-    if full and not args.no_tune:  # untimed: pick cell size and ray-pass variant
+    if args.method == "interp" and not args.no_tune:  # untimed: pick cell size and ray-pass variant
         t0 = time.perf_counter()
         params, res = irs.irs_autotune(params, dxy, dm)
         tune = {"cell_mult": res.cell_mult, "kernel_variant": res.kernel_variant,
@@ -195,6 +213,13 @@ def run_ours(args):
                 "tuning_s": time.perf_counter() - t0}
     plan = irs.Plan(params)
     info = plan.info
+    learned = None
+    if args.method == "mlp":  # untimed: train the network on this lens field
+        rep = irs.irs_mlp_train(plan.handle, dxy, dm, seed=11)
+        learned = {"samples": rep.samples, "steps": rep.steps, "loss_first": rep.loss_first,
+                   "loss_final": rep.loss_final, "heldout_rel_rms": rep.valid_rel_rms,
+                   "target_rms_thetaE": rep.target_rms, "ms_samples": rep.ms_samples,
+                   "ms_train": rep.ms_train}
     shape = (w["npix"], w["npix"])
     counts = torch.zeros(shape, dtype=torch.uint32, device=dev)
     mag = torch.zeros(shape, dtype=torch.float32, device=dev)
@@ -239,12 +264,10 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     my_ms = float(np.sum(step_ms))
     if world > 1:
-        tt = torch.tensor([my_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        my_ms = float(tt.item())
+        my_ms = slowest_rank_ms(my_ms, dist, dev)
         dist.barrier()
     ms_per_step = my_ms / args.steps
-    value = rays_per_step * world / (ms_per_step * 1e-3)
+    value = whole_job_rays_per_s(rays_per_step, world, ms_per_step)
 
     # ---- end to end through the public API with host buffers
     h_xy = torch.from_numpy(xy).pin_memory()
@@ -294,6 +317,20 @@ def run_ours(args):
     brute = None
     if full and not args.no_brute and rank == 0:
         brute = brute_band(irs, torch, w, xy, m, dxy, dm, band, plan, n_sms, peak_tflops, value)
+    if learned is not None and rank == 0:
+        # the series form on the same workload, and its error on the same band
+        pi = irs.Plan(workload_params(irs, "interp", w))
+        irs.irs_plan_set_timing(pi.handle, True)
+        ms = []
+        for k in range(3):
+            irs.irs_make_map(pi.handle, dxy, dm, counts, mag)
+            t = irs.irs_plan_timings(pi.handle)
+            if k:
+                ms.append(t.ms_total)
+        learned["interp_rays_per_s"] = info.n_rays / (float(np.mean(ms)) * 1e-3)
+        if brute is not None:
+            learned["interp_map_rel_rms_vs_brute"] = band_rel_rms(irs, torch, pi, dxy, dm, band, shape)
+        pi.close()
 
     if rank == 0:
         cpu = cpu_baseline(xy, m, w) if (world == 1 and not args.no_cpu) else None
@@ -314,6 +351,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "autotune": tune,
+            "learned": learned,
             "roofline": roofline,
             "clocks": clocks,
             "stage_ms": {"raypass_mean": ray_ms_mean, "map_total_mean": float(np.mean(tot_ms)),
@@ -325,6 +363,21 @@ def run_ours(args):
     plan.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+BRUTE_BAND_MAP = {}
+
+
+def band_rel_rms(irs, torch, plan, dxy, dm, band, shape):
+    """Per-pixel magnification rel RMS of `plan` against the last brute band map."""
+    a = BRUTE_BAND_MAP["counts"]
+    c = torch.zeros(shape, dtype=torch.uint32, device=dxy.device)
+    irs.irs_make_map_rows(plan.handle, dxy, dm, band[0], band[1], c)
+    plan.sync()
+    b = c.cpu().numpy().astype(np.float64)
+    sel = a >= 100
+    r = (b[sel] - a[sel]) / a[sel]
+    return float(np.sqrt(np.mean(r * r))) if sel.any() else None
 
 
 def brute_band(irs, torch, w, xy, m, dxy, dm, band, plan_fast, n_sms, peak_tflops, fast_value):
@@ -357,6 +410,7 @@ def brute_band(irs, torch, w, xy, m, dxy, dm, band, plan_fast, n_sms, peak_tflop
     rel = (b[sel] - a[sel]) / a[sel]
     pb.close()
     value = rays / (tot * 1e-3)
+    BRUTE_BAND_MAP["counts"] = a
     return {"value": value, "unit": "rays/s", "band_rows": [int(band[0]), int(band[1])],
             "rays": int(rays), "ms_per_band": tot,
             "roofline": {"bound": "alu", "kernel": "k_brute", "achieved": ach, "peak": peak_tflops,
