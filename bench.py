@@ -38,6 +38,11 @@ WORKLOAD = dict(name="paper-mid: kappa*=0.45 kappa_s=0 gamma=0.45, 1e5 Salpeter 
                      "2000^2 px over 20x20 thetaE, 100 rays/px",
                 kappa_star=0.45, kappa_s=0.0, gamma=0.45, S=20.0, npix=2000, nav=100.0,
                 n_star=100000, shape="salpeter", seed=2)
+# high resolution: 1e6 lenses, 1e8-pixel map (count map larger than L2)
+WORKLOAD_HIGHRES = dict(name="high-res: kappa*=0.35 kappa_s=0.15 gamma=0.4, 1e6 uniform lenses 0.1-1, "
+                             "10000^2 px over 25x25 thetaE, 40 rays/px",
+                        kappa_star=0.35, kappa_s=0.15, gamma=0.4, S=25.0, npix=10000, nav=40.0,
+                        n_star=1000000, shape="uniform", seed=3)
 # the learned far field's workload
 WORKLOAD_LEARNED = dict(name="learned: kappa*=0.4 kappa_s=0.1 gamma=0.35, 2e5 equal-mass lenses, "
                              "4000^2 px over 20x20 thetaE, 64 rays/px",
@@ -187,7 +192,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(local)
     n_sms = props.multi_processor_count
-    w = dict(WORKLOAD_LEARNED if args.method == "mlp" else WORKLOAD)
+    named = {"paper-mid": WORKLOAD, "high-res": WORKLOAD_HIGHRES, "learned": WORKLOAD_LEARNED}
+    w = dict(named[args.workload] if args.workload else
+             (WORKLOAD_LEARNED if args.method == "mlp" else WORKLOAD))
     if args.n_star:
         w["n_star"] = args.n_star
     if args.npix:
@@ -204,7 +211,9 @@ def run_ours(args):
     dxy = torch.from_numpy(xy).to(dev)
     dm = torch.from_numpy(m).to(dev)
     tune = None
-    if args.method == "interp" and not args.no_tune:  # untimed: pick cell size and ray-pass variant
+    if args.variant >= 0:
+        params.kernel_variant = args.variant
+    elif args.method == "interp" and not args.no_tune:  # untimed: pick cell size and ray-pass variant
         t0 = time.perf_counter()
         params, res = irs.irs_autotune(params, dxy, dm)
         tune = {"cell_mult": res.cell_mult, "kernel_variant": res.kernel_variant,
@@ -497,6 +506,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-brute", action="store_true", help="skip the brute-force band")
     ap.add_argument("--no-tune", action="store_true", help="paper-rule cells, default ray pass")
+    ap.add_argument("--variant", type=int, default=-1, help="fixed kernel variant (skips tuning)")
+    ap.add_argument("--workload", default="", choices=["", "paper-mid", "high-res", "learned"],
+                    help="default: paper-mid (learned for --method mlp)")
     ap.add_argument("--band-rows", type=int, default=0, help="brute band height (rows)")
     ap.add_argument("--n-star", type=int, default=0, help="override the lens count (profiling)")
     ap.add_argument("--npix", type=int, default=0, help="override the map side (profiling)")

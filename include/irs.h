@@ -74,8 +74,8 @@ typedef struct irs_params {
   double cell_mult;       /* INTERP: level-1 cell side in units of the paper's rule; 0 = default */
   int32_t window;         /* INTERP: cells within this Chebyshev distance sum lenses directly into
                              the series; 0 = default */
-  int32_t kernel_variant; /* INTERP: ray-pass variant 0..3 (rays per thread, level-2 sub-cells,
-                             sub-cell terms: 0 = 8/8/8, 1 = 8/16/6, 2 = 4/8/8, 3 = 4/16/6) */
+  int32_t kernel_variant; /* INTERP: ray-pass variant 0..9 (rays per thread, level-2 sub-cells,
+                             sub-cell terms, CTAs per SM, binning); irs_autotune picks one */
   int32_t reserved[6];    /* must be 0 */
 } irs_params;
 

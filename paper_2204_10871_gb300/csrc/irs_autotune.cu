@@ -2,8 +2,9 @@
 // variant of the interpolated method by timing them on the caller's lenses.
 //
 // Candidates: cell multiplier (of the paper's Delta x1 rule) in {0.5, 0.71,
-// 1, 1.41, 2} times the four ray-pass variants (rays per thread, level-2
-// sub-cells, sub-cell terms).  Each candidate plan makes one warm-up and one
+// 1, 1.41, 2} times the ray-pass variants (rays per thread, level-2 sub-cells,
+// sub-cell terms, CTAs per SM, binning), skipping cells wider than both
+// 2 theta_E and the paper rule's cell (FP32 near-field precision).  Each candidate plan makes one warm-up and one
 // timed map restricted to a band of lattice rows holding about 2e9 rays (the
 // whole lattice when smaller); its cost per map is the measured cell-list and
 // far-field time plus the ray-pass time scaled to the full lattice.  Results
@@ -22,7 +23,7 @@
 namespace {
 
 const double CELL_MULTS[] = {0.5, 0.70710678, 1.0, 1.41421356, 2.0};
-constexpr int NVARIANT = 4;
+constexpr int NVARIANT = 10;
 constexpr double BAND_RAYS = 2.0e9;
 std::mutex g_file_mu;
 
@@ -75,8 +76,14 @@ void cache_store(const char* path, const std::string& key, double mult, int vari
 
 // Estimated milliseconds per full map for one candidate, or a negative value
 // when the candidate cannot be planned.
+// Largest level-1 cell side a candidate may have: FP32 cell-relative
+// coordinates carry ~h 2^-24 of position error, which a lens at distance r
+// amplifies by m / r^2 in the near sum; beyond 2 theta_E (or the paper rule's
+// own cell, if larger) near-lens rays would lose the 1e-5 theta_E precision.
+constexpr double MAX_CELL_SIDE = 2.0;
+
 double measure(const irs_params& base, double mult, int variant, const double* xy, const double* mass,
-               int64_t n, uint32_t* counts, cudaStream_t s) {
+               int64_t n, uint32_t* counts, double h_rule, cudaStream_t s) {
   irs_params p = base;
   p.method = IRS_INTERP;
   p.cell_mult = mult;
@@ -85,6 +92,10 @@ double measure(const irs_params& base, double mult, int variant, const double* x
   if (irs_plan(&p, s, &P) != IRS_OK) return -1.0;
   irs_plan_info info;
   irs_plan_info_get(P, &info);
+  if (info.cell_x > fmax(MAX_CELL_SIDE, h_rule) * (1.0 + 1e-9)) {
+    irs_plan_destroy(P);
+    return -1.0;
+  }
   int64_t rows = (int64_t)ceil(BAND_RAYS / (double)info.n_rays_x);
   if (rows < 2 * info.rays_per_cell_y) rows = 2 * info.rays_per_cell_y;
   if (rows > info.n_rays_y) rows = info.n_rays_y;
@@ -140,10 +151,25 @@ extern "C" irs_status irs_autotune(const irs_params* params, const double* lens_
     cudaGetLastError();
     return IRS_ERR_OOM;
   }
+  // the paper rule's cell side, the reference for the size guard
+  double h_rule = 0.0;
+  {
+    irs_params p = *params;
+    p.method = IRS_INTERP;
+    p.cell_mult = 1.0;
+    p.kernel_variant = 0;
+    irs_plan_t* P = nullptr;
+    if (irs_plan(&p, s, &P) == IRS_OK) {
+      irs_plan_info info;
+      irs_plan_info_get(P, &info);
+      h_rule = info.cell_x;
+      irs_plan_destroy(P);
+    }
+  }
   double best = -1.0;
   for (double m : CELL_MULTS) {
     for (int v = 0; v < NVARIANT; ++v) {
-      const double t = measure(*params, m, v, lens_xy, mass, n, counts, s);
+      const double t = measure(*params, m, v, lens_xy, mass, n, counts, h_rule, s);
       if (t < 0) continue;
       r.candidates++;
       if (m == 1.0 && v == 0) r.ms_default = t;

@@ -127,7 +127,7 @@ irs_status build_entry(BatchEntry* e, irs_plan_t* const* plans, int32_t nmaps,
     if (cudaEventCreateWithFlags(&e->ev[k], cudaEventDisableTiming) != cudaSuccess) return IRS_ERR_CUDA;
 
   // interpolated maps grouped by ray-pass variant; descriptors + queues in one buffer
-  std::vector<std::vector<int>> groups(4);
+  std::vector<std::vector<int>> groups(10);
   for (int32_t m = 0; m < nmaps; ++m)
     if (plans[m]->p.method != IRS_BRUTE) groups[irs::interp_variant(plans[m])].push_back(m);
   std::vector<size_t> group_off(groups.size(), 0);

@@ -172,13 +172,21 @@ cudaError_t launch_brute_setup(const irs_plan_t* P, cudaStream_t s) {
 // ------------------------------------------------------------ ray pass
 enum { MODE_MAP = 0, MODE_DUMP = 1 };
 
-template <int MODE>
-__global__ void __launch_bounds__(BR_THREADS, 2)
+// Variants: R rows per thread (the tile stays 32 x 64: 64/R warps per CTA) and
+// PAIRED rows per thread that share one reciprocal per two rows.  The TwoSum
+// accumulators live in shared memory (updated once per 256-lens stage).
+#define BR_VARIANTS(X) X(0, 16, 8) X(1, 8, 4) X(2, 8, 2) X(3, 16, 4) X(4, 16, 2)
+constexpr int BR_NVARIANT = 5;
+
+template <int MODE, int R, int PAIRED>
+__global__ void __launch_bounds__(32 * (BR_TY / R), 512 / (32 * (BR_TY / R)))
 k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, int64_t n,
         const TileRec* __restrict__ recs, int64_t ntx, int64_t nwork, int64_t row0, int64_t row1,
         uint32_t* __restrict__ counts, const int64_t* __restrict__ idx,
         double* __restrict__ beta_out, int64_t* __restrict__ pix_out) {
+  constexpr int NT = 32 * (BR_TY / R);
   __shared__ float4 lens_s[BR_LT];
+  __shared__ float acc_s[4][R][NT];  // x hi, x lo, y hi, y lo
   __shared__ TileRec rec;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -203,31 +211,34 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
     const double zx = g.a1 + tg.ci * g.dx3, zy = g.b1 + tg.cj * g.dx3;
     const int64_t col = tg.i0 + lane;
     const float tx = (float)(((double)col + 0.5 - tg.ci) * g.dx3);
-    float ty[BR_R];
+    float ty[R];
 #pragma unroll
-    for (int r = 0; r < BR_R; ++r)
-      ty[r] = (float)(((double)(tg.j0 + warp * BR_R + r) + 0.5 - tg.cj) * g.dx3);
-
-    float axh[BR_R], axl[BR_R], ayh[BR_R], ayl[BR_R];
-#pragma unroll
-    for (int r = 0; r < BR_R; ++r) axh[r] = axl[r] = ayh[r] = ayl[r] = 0.f;
+    for (int r = 0; r < R; ++r) {
+      ty[r] = (float)(((double)(tg.j0 + warp * R + r) + 0.5 - tg.cj) * g.dx3);
+      acc_s[0][r][tid] = acc_s[1][r][tid] = acc_s[2][r][tid] = acc_s[3][r][tid] = 0.f;
+    }
 
     __syncthreads();  // previous tile's readers of rec / lens_s are done
     if (tid == 0) rec = recs[tile];
 
     for (int64_t base = 0; base < n; base += BR_LT) {
-      const int64_t k = base + tid;
-      float4 v = make_float4(1.0e15f, 1.0e15f, 0.f, 0.f);  // padding: massless, far away
-      if (k < n) {
-        const double2 p = xy[k];
-        v = make_float4((float)(p.x - zx), (float)(p.y - zy), (float)mass[k], 0.f);
+      float4 v[BR_LT / NT];
+#pragma unroll
+      for (int q = 0; q < BR_LT / NT; ++q) {
+        const int64_t k = base + q * NT + tid;
+        v[q] = make_float4(1.0e15f, 1.0e15f, 0.f, 0.f);  // padding: massless, far away
+        if (k < n) {
+          const double2 p = xy[k];
+          v[q] = make_float4((float)(p.x - zx), (float)(p.y - zy), (float)mass[k], 0.f);
+        }
       }
       __syncthreads();
-      lens_s[tid] = v;
-      __syncthreads();
-      float pax[BR_R], pay[BR_R];
 #pragma unroll
-      for (int r = 0; r < BR_R; ++r) pax[r] = pay[r] = 0.f;
+      for (int q = 0; q < BR_LT / NT; ++q) lens_s[q * NT + tid] = v[q];
+      __syncthreads();
+      float pax[R], pay[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) pax[r] = pay[r] = 0.f;
       // lenses in this stage, rounded up to the unroll (padding is massless)
       const int cnt = (int)min((int64_t)BR_LT, ((n - base) + 7) & ~(int64_t)7);
 #pragma unroll 2
@@ -235,10 +246,10 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
         const float4 L = lens_s[jl];
         const float dx = tx - L.x;
         const float dx2 = dx * dx;
-        // rows 0..BR_PAIRED-1: one reciprocal for two rows, 1/(r_a^2 r_b^2), to move
+        // rows 0..PAIRED-1: one reciprocal for two rows, 1/(r_a^2 r_b^2), to move
         // work from the SFU (MUFU) to the FP32 pipe; remaining rows: one each
 #pragma unroll
-        for (int r = 0; r < BR_PAIRED; r += 2) {
+        for (int r = 0; r < PAIRED; r += 2) {
           const float dya = ty[r] - L.y, dyb = ty[r + 1] - L.y;
           const float r2a = fmaf(dya, dya, dx2), r2b = fmaf(dyb, dyb, dx2);
           const float mR = L.z * rcp_approx(r2a * r2b);
@@ -249,7 +260,7 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
           pay[r + 1] = fmaf(wb, dyb, pay[r + 1]);
         }
 #pragma unroll
-        for (int r = BR_PAIRED; r < BR_R; ++r) {
+        for (int r = PAIRED; r < R; ++r) {
           const float dy = ty[r] - L.y;
           const float r2 = fmaf(dy, dy, dx2);
           const float w = L.z * rcp_approx(r2);
@@ -258,22 +269,22 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
         }
       }
 #pragma unroll
-      for (int r = 0; r < BR_R; ++r) {
+      for (int r = 0; r < R; ++r) {
         float s, e;
-        two_sum(axh[r], pax[r], s, e);
-        axh[r] = s;
-        axl[r] += e;
-        two_sum(ayh[r], pay[r], s, e);
-        ayh[r] = s;
-        ayl[r] += e;
+        two_sum(acc_s[0][r][tid], pax[r], s, e);
+        acc_s[0][r][tid] = s;
+        acc_s[1][r][tid] += e;
+        two_sum(acc_s[2][r][tid], pay[r], s, e);
+        acc_s[2][r][tid] = s;
+        acc_s[3][r][tid] += e;
       }
     }
     __syncthreads();  // rec visible
 
     // ---- per-ray: smooth terms, sheet series, near corners, pixel
 #pragma unroll
-    for (int r = 0; r < BR_R; ++r) {
-      const int64_t row = tg.j0 + warp * BR_R + r;
+    for (int r = 0; r < R; ++r) {
+      const int64_t row = tg.j0 + warp * R + r;
       const bool inside = (col < tg.i1) && (row < tg.j1) && (row >= row0) && (row < row1);
       // P(t) = sum_n T_n t^n by Horner, complex FP32
       float pr = 0.f, pi = 0.f;
@@ -290,11 +301,13 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
         pr += rec.near[c][2] * pli;                                    // -i a_c (w Log w)
         pi -= rec.near[c][2] * plr;
       }
+      const float axh = acc_s[0][r][tid], axl = acc_s[1][r][tid];
+      const float ayh = acc_s[2][r][tid], ayl = acc_s[3][r][tid];
       float s1, e1, s2, e2;
-      two_sum(rec.cx_hi, -axh[r], s1, e1);
-      two_sum(rec.cy_hi, -ayh[r], s2, e2);
-      const float b1 = s1 + (((e1 + rec.cx_lo) - axl[r]) + (g.lam_s1 * tx + pr));
-      const float b2 = s2 + (((e2 + rec.cy_lo) - ayl[r]) + (g.lam_s2 * ty[r] - pi));
+      two_sum(rec.cx_hi, -axh, s1, e1);
+      two_sum(rec.cy_hi, -ayh, s2, e2);
+      const float b1 = s1 + (((e1 + rec.cx_lo) - axl) + (g.lam_s1 * tx + pr));
+      const float b2 = s2 + (((e2 + rec.cy_lo) - ayl) + (g.lam_s2 * ty[r] - pi));
       uint32_t key = 0;
       int64_t pix = -1;
       const bool ok = inside && pixel_from_rel(g, rec.ix, rec.iy, b1, b2, key, pix);
@@ -311,13 +324,38 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
   }
 }
 
-int brute_grid_size(int num_sms) {
+#define BR_DECL_OCC(V, R, PAIRED)                                                               \
+  case V:                                                                                       \
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_brute<MODE_MAP, R, PAIRED>,    \
+                                                      32 * (BR_TY / R), 0) != cudaSuccess)      \
+      per_sm = 1;                                                                               \
+    break;
+int brute_grid_size(int num_sms, int variant) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_brute<MODE_MAP>, BR_THREADS, 0) !=
-          cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  return num_sms * per_sm;
+  switch (variant) { BR_VARIANTS(BR_DECL_OCC) default: break; }
+  return num_sms * (per_sm < 1 ? 1 : per_sm);
+}
+
+#define BR_DECL_LAUNCH(V, R, PAIRED)                                                           \
+  case V:                                                                                      \
+    if (mode == MODE_MAP)                                                                      \
+      k_brute<MODE_MAP, R, PAIRED><<<(unsigned)grid, 32 * (BR_TY / R), 0, s>>>(                \
+          P->g, xy2, mass, n, P->d_tiles, P->br_ntx, nwork, row0, row1, counts, idx, beta, pix); \
+    else                                                                                       \
+      k_brute<MODE_DUMP, R, PAIRED><<<(unsigned)grid, 32 * (BR_TY / R), 0, s>>>(               \
+          P->g, xy2, mass, n, P->d_tiles, P->br_ntx, nwork, row0, row1, counts, idx, beta, pix); \
+    break;
+static cudaError_t launch_brute(const irs_plan_t* P, int mode, int64_t grid, const double* xy,
+                                const double* mass, int64_t n, int64_t nwork, int64_t row0,
+                                int64_t row1, uint32_t* counts, const int64_t* idx, double* beta,
+                                int64_t* pix, cudaStream_t s) {
+  const double2* xy2 = reinterpret_cast<const double2*>(xy);
+  switch (P->p.kernel_variant) {
+    BR_VARIANTS(BR_DECL_LAUNCH)
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_brute_map(const irs_plan_t* P, const double* xy, const double* mass, int64_t n,
@@ -326,20 +364,15 @@ cudaError_t launch_brute_map(const irs_plan_t* P, const double* xy, const double
   const int64_t tr0 = row0 / BR_TY, tr1 = (row1 + BR_TY - 1) / BR_TY;
   const int64_t nwork = (tr1 - tr0) * P->br_ntx;
   const int64_t grid = nwork < P->br_grid ? nwork : P->br_grid;
-  k_brute<MODE_MAP><<<(unsigned)grid, BR_THREADS, 0, s>>>(
-      P->g, reinterpret_cast<const double2*>(xy), mass, n, P->d_tiles, P->br_ntx, nwork, row0,
-      row1, counts, nullptr, nullptr, nullptr);
-  return cudaGetLastError();
+  return launch_brute(P, MODE_MAP, grid, xy, mass, n, nwork, row0, row1, counts, nullptr, nullptr,
+                      nullptr, s);
 }
 
 cudaError_t launch_brute_dump(const irs_plan_t* P, const double* xy, const double* mass, int64_t n,
                               const int64_t* idx, int64_t nidx, double* beta, int64_t* pix,
                               cudaStream_t s) {
   const int64_t grid = nidx < P->br_grid ? nidx : P->br_grid;
-  k_brute<MODE_DUMP><<<(unsigned)grid, BR_THREADS, 0, s>>>(
-      P->g, reinterpret_cast<const double2*>(xy), mass, n, P->d_tiles, P->br_ntx, nidx, 0,
-      P->g.nry, nullptr, idx, beta, pix);
-  return cudaGetLastError();
+  return launch_brute(P, MODE_DUMP, grid, xy, mass, n, nidx, 0, P->g.nry, nullptr, idx, beta, pix, s);
 }
 
 // ------------------------------------------------------------ magnification

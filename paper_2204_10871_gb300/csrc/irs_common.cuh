@@ -60,6 +60,22 @@ __device__ __forceinline__ void bin_warp(uint32_t* counts, bool valid, uint32_t 
   if (valid && lane == __ffs(peers) - 1) atomicAdd(counts + key, (uint32_t)__popc(peers));
 }
 
+// Run-length variant: lanes hold consecutive columns of one row, so equal
+// pixels usually come in runs; the first lane of each run of equal valid keys
+// adds the run's length (non-adjacent equal keys add separately).
+__device__ __forceinline__ void bin_warp_runs(uint32_t* counts, bool valid, uint32_t key) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t k = valid ? key : 0xFFFFFFFFu;
+  const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, k, 1);
+  const bool head = (lane == 0) || (k != prev);
+  const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
+  if (valid && head) {
+    const unsigned later = heads & ~((2u << lane) - 1u);  // heads after this lane
+    const int next = later ? __ffs(later) - 1 : 32;
+    atomicAdd(counts + key, (uint32_t)(next - lane));
+  }
+}
+
 // Pixel of a ray from its position relative to the base pixel's lower-left
 // corner (brel1, brel2 in theta_E) -- reading R7, floor per axis.
 __device__ __forceinline__ bool pixel_from_rel(const Geo& g, int32_t ix, int32_t iy, float brel1,
@@ -79,20 +95,20 @@ __device__ __forceinline__ bool pixel_from_rel(const Geo& g, int32_t ix, int32_t
 // float offsets against the cell's base pixel (lo = -base, hi = npix - base),
 // so NaN / Inf / far-off rays fail it before any conversion.
 __device__ __forceinline__ bool pixel_fast(float brel1, float brel2, float inv_sx, float inv_sy,
-                                           float lo1, float hi1, float lo2, float hi2, int32_t ix,
+                                           int32_t lo1, int32_t hi1, int32_t lo2, int32_t hi2, int32_t ix,
                                            int32_t iy, int32_t npix_x, uint32_t& key) {
-  const float f1 = floorf(brel1 * inv_sx), f2 = floorf(brel2 * inv_sy);
-  const bool ok = (f1 >= lo1) && (f1 < hi1) && (f2 >= lo2) && (f2 < hi2);
-  key = ok ? (uint32_t)((iy + (int32_t)f2) * npix_x + (ix + (int32_t)f1)) : 0u;
+  const float t1 = brel1 * inv_sx, t2 = brel2 * inv_sy;
+  // finite and within int range (NaN fails both compares); then one round-down each
+  const bool fin = fabsf(t1) < 1.0e9f && fabsf(t2) < 1.0e9f;
+  const int32_t f1 = __float2int_rd(t1), f2 = __float2int_rd(t2);
+  const bool ok = fin && (f1 >= lo1) && (f1 < hi1) && (f2 >= lo2) && (f2 < hi2);
+  key = ok ? (uint32_t)((iy + f2) * npix_x + (ix + f1)) : 0u;
   return ok;
 }
 
 // ---------------------------------------------------------------- brute force
 constexpr int BR_TX = 32;             // tile columns: one per lane
-constexpr int BR_WARPS = 8;           // warps per CTA
-constexpr int BR_R = 8;               // rays (rows) per thread
-constexpr int BR_TY = BR_WARPS * BR_R;
-constexpr int BR_THREADS = BR_WARPS * 32;
+constexpr int BR_TY = 64;             // tile rows: 64/R warps of R rows per thread
 constexpr int BR_LT = 256;            // lenses per shared-memory stage (= FP32 partial length)
 constexpr int BR_PAIRED = 4;          // rows per thread that share one reciprocal per two rows
 constexpr int SHEET_TERMS = 8;        // Taylor terms t^1..t^8 of the sheet's analytic part
@@ -177,7 +193,7 @@ cudaError_t launch_brute_dump(const irs_plan_t* P, const double* xy, const doubl
                               const int64_t* idx, int64_t nidx, double* beta, int64_t* pix,
                               cudaStream_t s);
 cudaError_t launch_magnify(const irs_plan_t* P, const uint32_t* counts, float* mag, cudaStream_t s);
-int brute_grid_size(int num_sms);
+int brute_grid_size(int num_sms, int variant);
 // FP64 sizing of the plane and lattice (irs_api.cu)
 irs_status size_plane(irs_plan_t* P);
 }  // namespace irs

@@ -42,7 +42,8 @@ namespace {
 
 constexpr int IP_KMAX = 32;        // local series terms (max)
 constexpr int IP_P = 18;           // multipole terms and local terms produced by the M2L
-constexpr int IP_NEAR_MAX = 2048;  // lenses of a 3x3 block held in shared memory
+constexpr int IP_NEAR_MAX = 1024;  // lenses of a 3x3 block held in shared memory
+constexpr int IP_KMAX_RAYS = 1024;  // rays along a cell side (row table in shared memory)
 constexpr int IP_THREADS = 256;
 constexpr int IP_MAX_CORNER = 4;
 
@@ -451,17 +452,23 @@ struct IpRayArgs {
 // Q = 8 with 8 terms and Q = 16 with 6 terms both truncate below 1e-8 of the
 // nearest far lens's field (sub-cell half-diagonal / distance to it: 0.083
 // and 0.042).
-#define IP_VARIANTS(X) X(0, 8, 8, 8) X(1, 8, 16, 6) X(2, 4, 8, 8) X(3, 4, 16, 6)
-constexpr int IP_NVARIANT = 4;
+// MINB: CTAs per SM the register budget is sized for; BIN: warp binning by
+// __match_any_sync (0) or by runs of equal pixels (1).
+#define IP_VARIANTS(X)                                                                       \
+  X(0, 8, 8, 8, 2, 0) X(1, 8, 16, 6, 2, 0) X(2, 4, 8, 8, 2, 0) X(3, 4, 16, 6, 2, 0)           \
+  X(4, 8, 16, 6, 2, 1) X(5, 8, 16, 6, 3, 1) X(6, 4, 16, 6, 3, 1) X(7, 8, 16, 6, 3, 0)           \
+  X(8, 4, 16, 6, 4, 0) X(9, 8, 8, 8, 3, 0)
+constexpr int IP_NVARIANT = 10;
 
 // One level-1 cell: gather the 3x3 block's lenses, re-centre the series on the
 // sub-cells, then every ray of rows [jlo, jhi) of the cell.  In DUMP mode the
 // thread holding ray (want_i, want_j) writes its beta and pixel to slot `work`.
-template <int MODE, int R, int Q, int K2>
+template <int MODE, int R, int Q, int K2, int BIN>
 __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpRayArgs& a, int64_t rc,
                                         int64_t want_i, int64_t want_j, int64_t work) {
   __shared__ float4 near_s[IP_NEAR_MAX];
   __shared__ float2 sub_s[Q * Q][K2];
+  __shared__ float4 row_s[IP_KMAX_RAYS];  // per cell row: t_y, sigma_y, level-2 row offset (bits)
   __shared__ float2 c_s[IP_KMAX];
   __shared__ CellRec rec_s;
   __shared__ int blk_start[9], blk_off[10];
@@ -532,29 +539,43 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     const float sc = powf((float)Q, -(float)nn);
     sub_s[sub][nn] = make_float2(sr * sc, si * sc);
   }
+  // row table: t_y = tau_y h, sigma_y = (l + 1/2) Q / k - v - 1/2, v Q (level-2 row offset)
+  for (int l = tid; l < (int)(jhi - j0); l += blockDim.x) {
+    const float sv = ((float)l + 0.5f) * ((float)Q * inv_k);
+    const int v = min(__float2int_rd(sv), Q - 1);
+    row_s[l] = make_float4(fmaf((float)l, inv_k, 0.5f * inv_k - 0.5f) * hf, sv - (float)v - 0.5f,
+                           __int_as_float(v * Q), 0.f);
+  }
   __syncthreads();
 
   // base-pixel range of this cell for the 32-bit pixel test
-  const float lo1 = (float)(-rec_s.ix), hi1 = (float)(g.npix_x - rec_s.ix);
-  const float lo2 = (float)(-rec_s.iy), hi2 = (float)(g.npix_y - rec_s.iy);
+  const int32_t lo1 = -rec_s.ix, hi1 = g.npix_x - rec_s.ix;
+  const int32_t lo2 = -rec_s.iy, hi2 = g.npix_y - rec_s.iy;
+  const float bxh = rec_s.bx_hi, bxl = rec_s.bx_lo, byh = rec_s.by_hi, byl = rec_s.by_lo;
+  const int n_corner = rec_s.n_corner;
+  const int32_t rix = rec_s.ix, riy = rec_s.iy;
+  // cell-local 32-bit lattice indices: columns [0, kx), rows [ylo, yhi)
+  const int kx = (int)(i1 - i0), ylo = (int)(jlo - j0), yhi = (int)(jhi - j0);
+  const float c_tau = 0.5f * inv_k - 0.5f;  // tau = (l + 1/2)/k - 1/2
+  const float qk = (float)Q * inv_k;        // sub-cell index = floor((l + 1/2) Q / k)
   // work units (32-column strip x R-row group), dealt round-robin to warps
   const int nwarps = blockDim.x / 32;
-  const int nstrip = (int)((i1 - i0 + 31) / 32);
-  const int nrg = (int)((jhi - jlo + R - 1) / R);
+  const int nstrip = (kx + 31) / 32;
+  const int nrg = (yhi - ylo + R - 1) / R;
   const int nunit = nstrip * nrg;
   for (int unit = warp; unit < nunit; unit += nwarps) {
     const int st = unit % nstrip, rg = unit / nstrip;
-    const int64_t col = i0 + (int64_t)st * 32 + lane;
-    const int64_t r0 = jlo + (int64_t)rg * R;
-    const float taux = ((float)(col - i0) + 0.5f) * inv_k - 0.5f;
+    const int cl = st * 32 + lane;
+    const int rl0 = ylo + rg * R;
+    const float taux = fmaf((float)cl, inv_k, c_tau);
     const float tx = taux * hf;
-    int u = (int)floorf((taux + 0.5f) * Q);
-    u = u < 0 ? 0 : (u >= Q ? Q - 1 : u);
-    const float sgr = (taux - (((float)u + 0.5f) / Q - 0.5f)) * Q;
+    const float su = ((float)cl + 0.5f) * qk;
+    const int u = min(__float2int_rd(su), Q - 1);
+    const float sgr = su - (float)u - 0.5f;
     float ty[R], ax[R], ay[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      ty[r] = (((float)(r0 + r - j0) + 0.5f) * inv_k - 0.5f) * hf;
+      ty[r] = row_s[min(rl0 + r, yhi - 1)].x;  // rows past the cell end are masked later
       ax[r] = ay[r] = 0.f;
     }
 #pragma unroll 2
@@ -573,14 +594,12 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int64_t row = r0 + r;
-      const bool inside = col < i1 && row < jhi;
-      // sub-cell and its series in sigma = (tau - eps) Q
-      const float tauy = ((float)(row - j0) + 0.5f) * inv_k - 0.5f;
-      int v = (int)floorf((tauy + 0.5f) * Q);
-      v = v < 0 ? 0 : (v >= Q ? Q - 1 : v);
-      const float sgi = (tauy - (((float)v + 0.5f) / Q - 0.5f)) * Q;
-      const float2* d = sub_s[v * Q + u];
+      const int rl = rl0 + r;
+      const bool inside = cl < kx && rl < yhi;
+      // sub-cell and its series in sigma = (tau - eps) Q = (l + 1/2) Q / k - v - 1/2
+      const float4 rw = row_s[min(rl, yhi - 1)];
+      const float sgi = rw.y;
+      const float2* d = sub_s[__float_as_int(rw.z) + u];
       float pr = d[K2 - 1].x, pi = d[K2 - 1].y;
 #pragma unroll
       for (int nn = K2 - 2; nn >= 0; --nn) {
@@ -590,23 +609,26 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
         pr = nr;
         pi = ni;
       }
-      for (int q = 0; q < rec_s.n_corner; ++q) {
-        const float wr = rec_s.corner[q][0] + tx, wi = rec_s.corner[q][1] + ty[r];
-        const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
-        const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
-        pr += rec_s.corner[q][2] * pli;
-        pi -= rec_s.corner[q][2] * plr;
+      if (n_corner) {
+        for (int q = 0; q < n_corner; ++q) {
+          const float wr = rec_s.corner[q][0] + tx, wi = rec_s.corner[q][1] + ty[r];
+          const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
+          const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
+          pr += rec_s.corner[q][2] * pli;
+          pi -= rec_s.corner[q][2] * plr;
+        }
       }
-      const float b1 = rec_s.bx_hi + ((rec_s.bx_lo - ax[r]) + (g.lam_s1 * tx + pr));
-      const float b2 = rec_s.by_hi + ((rec_s.by_lo - ay[r]) + (g.lam_s2 * ty[r] - pi));
+      const float b1 = bxh + ((bxl - ax[r]) + (g.lam_s1 * tx + pr));
+      const float b2 = byh + ((byl - ay[r]) + (g.lam_s2 * ty[r] - pi));
       uint32_t key;
-      const bool ok = pixel_fast(b1, b2, g.inv_sx, g.inv_sy, lo1, hi1, lo2, hi2, rec_s.ix, rec_s.iy,
-                                 g.npix_x, key) && inside;
+      const bool ok =
+          pixel_fast(b1, b2, g.inv_sx, g.inv_sy, lo1, hi1, lo2, hi2, rix, riy, g.npix_x, key) && inside;
       if (MODE == IP_MAP) {
-        bin_warp(a.counts, ok, key);
-      } else if (col == want_i && row == want_j) {
-        a.beta_out[2 * work] = (g.src_x0 + (double)rec_s.ix * g.sx) + (double)b1;
-        a.beta_out[2 * work + 1] = (g.src_y0 + (double)rec_s.iy * g.sy) + (double)b2;
+        if (BIN) bin_warp_runs(a.counts, ok, key);
+        else bin_warp(a.counts, ok, key);
+      } else if (i0 + cl == want_i && j0 + rl == want_j) {
+        a.beta_out[2 * work] = (g.src_x0 + (double)rix * g.sx) + (double)b1;
+        a.beta_out[2 * work + 1] = (g.src_y0 + (double)riy * g.sy) + (double)b2;
         if (a.pix_out) a.pix_out[work] = ok ? (int64_t)key : -1;
       }
     }
@@ -614,11 +636,11 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
 }
 
 // One map: persistent grid over its ray cells (MAP) or requested rays (DUMP).
-template <int MODE, int R, int Q, int K2>
-__global__ void __launch_bounds__(IP_THREADS, 2) k_ip_ray(Geo g, IpGeo ig, IpRayArgs a) {
+template <int MODE, int R, int Q, int K2, int MINB, int BIN>
+__global__ void __launch_bounds__(IP_THREADS, MINB) k_ip_ray(Geo g, IpGeo ig, IpRayArgs a) {
   for (int64_t work = blockIdx.x; work < a.nwork; work += gridDim.x) {
     if (MODE == IP_MAP) {
-      ip_cell<IP_MAP, R, Q, K2>(g, ig, a, a.rc_base + work, -1, -1, work);
+      ip_cell<IP_MAP, R, Q, K2, BIN>(g, ig, a, a.rc_base + work, -1, -1, work);
     } else {
       const int64_t f = a.idx[work];
       if (f < 0 || f >= g.nrx * g.nry) {  // not a lattice ray: report it, touch nothing else
@@ -629,7 +651,7 @@ __global__ void __launch_bounds__(IP_THREADS, 2) k_ip_ray(Geo g, IpGeo ig, IpRay
         continue;
       }
       const int64_t wi = f % g.nrx, wj = f / g.nrx;
-      ip_cell<IP_DUMP, R, Q, K2>(g, ig, a, (wj / ig.k) * ig.nrcx + wi / ig.k, wi, wj, work);
+      ip_cell<IP_DUMP, R, Q, K2, BIN>(g, ig, a, (wj / ig.k) * ig.nrcx + wi / ig.k, wi, wj, work);
     }
   }
 }
@@ -643,8 +665,8 @@ struct MapDesc {
   int64_t item0;  // index of the map's first item in the concatenated list
 };
 
-template <int R, int Q, int K2>
-__global__ void __launch_bounds__(IP_THREADS, 2)
+template <int R, int Q, int K2, int MINB, int BIN>
+__global__ void __launch_bounds__(IP_THREADS, MINB)
 k_ip_ray_batch(const MapDesc* __restrict__ maps, int nmaps, int64_t nitems,
                unsigned long long* __restrict__ queue) {
   __shared__ MapDesc md;
@@ -671,14 +693,14 @@ k_ip_ray_batch(const MapDesc* __restrict__ maps, int nmaps, int64_t nitems,
     __syncthreads();
     const long long it = item_s;
     if (it >= nitems) break;
-    ip_cell<IP_MAP, R, Q, K2>(md.g, md.ig, md.a, md.a.rc_base + (it - md.item0), -1, -1, it);
+    ip_cell<IP_MAP, R, Q, K2, BIN>(md.g, md.ig, md.a, md.a.rc_base + (it - md.item0), -1, -1, it);
   }
 }
 
-#define IP_DECL_OCC(V, R, Q, K2)                                                     \
-  case V:                                                                           \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP, R, Q, K2>, \
-                                                  IP_THREADS, 0);                   \
+#define IP_DECL_OCC(V, R, Q, K2, MINB, BIN)                                                       \
+  case V:                                                                                         \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN>, \
+                                                  IP_THREADS, 0);                                 \
     break;
 int ip_ray_occupancy(int variant) {
   int per_sm = 0;
@@ -686,12 +708,12 @@ int ip_ray_occupancy(int variant) {
   return per_sm > 0 ? per_sm : 1;
 }
 
-#define IP_DECL_LAUNCH(V, R, Q, K2)                                                 \
-  case V:                                                                          \
-    if (mode == IP_MAP)                                                            \
-      k_ip_ray<IP_MAP, R, Q, K2><<<(unsigned)grid, IP_THREADS, 0, s>>>(g, ig, a);  \
-    else                                                                           \
-      k_ip_ray<IP_DUMP, R, Q, K2><<<(unsigned)grid, IP_THREADS, 0, s>>>(g, ig, a); \
+#define IP_DECL_LAUNCH(V, R, Q, K2, MINB, BIN)                                                \
+  case V:                                                                                     \
+    if (mode == IP_MAP)                                                                       \
+      k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, 0, s>>>(g, ig, a);  \
+    else                                                                                      \
+      k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, 0, s>>>(g, ig, a); \
     break;
 cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, const Geo& g,
                           const IpGeo& ig, const IpRayArgs& a) {
@@ -699,9 +721,10 @@ cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, c
   return cudaGetLastError();
 }
 
-#define IP_DECL_BATCH(V, R, Q, K2)                                                          \
-  case V:                                                                                  \
-    k_ip_ray_batch<R, Q, K2><<<(unsigned)grid, IP_THREADS, 0, s>>>(maps, nmaps, nitems, queue); \
+#define IP_DECL_BATCH(V, R, Q, K2, MINB, BIN)                                                \
+  case V:                                                                                    \
+    k_ip_ray_batch<R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, 0, s>>>(maps, nmaps,       \
+                                                                             nitems, queue); \
     break;
 cudaError_t launch_ip_ray_batch(int variant, int64_t grid, cudaStream_t s, const MapDesc* maps,
                                 int nmaps, int64_t nitems, unsigned long long* queue) {
@@ -839,7 +862,7 @@ irs_status interp_plan(irs_plan_t* P) {
   double dx1 = fmin(L0, fmin(Ix, Iy) / 10.0) * (p.cell_mult > 0 ? p.cell_mult : 1.0);
   int64_t k = (int64_t)ceil(dx1 / g.dx3 - 1e-9);
   if (k < 4) k = 4;
-  if (k > (int64_t)1 << 20) return IRS_ERR_OVERFLOW;
+  if (k > IP_KMAX_RAYS) k = IP_KMAX_RAYS;  // the ray pass keeps a row table per cell
   ig.k = k;
   ig.h = (double)k * g.dx3;
   ig.nrcx = (int32_t)((g.nrx + k - 1) / k);

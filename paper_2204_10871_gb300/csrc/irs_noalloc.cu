@@ -55,7 +55,7 @@ irs_status device_setup(int dev, char** scratch, int* num_sms, int* grid) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return IRS_ERR_CUDA;
     g_num_sms[dev] = sms;
-    g_grid[dev] = irs::brute_grid_size(sms);
+    g_grid[dev] = irs::brute_grid_size(sms, 0);
     g_scratch_addr[dev] = ptr;
   }
   *scratch = static_cast<char*>(g_scratch_addr[dev]);
@@ -81,6 +81,7 @@ extern "C" irs_status irs_make_map_brute_noalloc(const irs_params* params, const
   if (p.kappa_star < 0 || p.kappa_s < 0 || p.flags != 0) return IRS_ERR_ARG;
   if (p.plane != IRS_PLANE_RECT && p.plane != IRS_PLANE_CIRCLE) return IRS_ERR_ARG;
   if (p.method != IRS_BRUTE) return IRS_ERR_UNSUPPORTED;
+  if (p.kernel_variant != 0) return IRS_ERR_UNSUPPORTED;  // the default brute kernel only
   if (n < 0 || (n > 0 && (!lens_xy || !mass)) || (n > 0 && ((uintptr_t)lens_xy & 15u)))
     return IRS_ERR_ARG;
   if (n > ((int64_t)1 << 31)) return IRS_ERR_OVERFLOW;
