@@ -91,13 +91,12 @@ __device__ __forceinline__ bool pixel_from_rel(const Geo& g, int32_t ix, int32_t
   return true;
 }
 
-// Pixel of a ray in 32-bit arithmetic: the range test is done on the floored
-// float offsets against the cell's base pixel (lo = -base, hi = npix - base),
-// so NaN / Inf / far-off rays fail it before any conversion.
-__device__ __forceinline__ bool pixel_fast(float brel1, float brel2, float inv_sx, float inv_sy,
-                                           int32_t lo1, int32_t hi1, int32_t lo2, int32_t hi2, int32_t ix,
-                                           int32_t iy, int32_t npix_x, uint32_t& key) {
-  const float t1 = brel1 * inv_sx, t2 = brel2 * inv_sy;
+// Pixel of a ray in 32-bit arithmetic from its offset to the base pixel in
+// pixel units (t = beta_rel / s): NaN, Inf and far-off rays fail the finiteness
+// test, the rest are floored and range-tested against the cell's base pixel
+// (lo = -base, hi = npix - base).
+__device__ __forceinline__ bool pixel_scaled(float t1, float t2, int32_t lo1, int32_t hi1, int32_t lo2,
+                                             int32_t hi2, int32_t ix, int32_t iy, int32_t npix_x, uint32_t& key) {
   // finite and within int range (NaN fails both compares); then one round-down each
   const bool fin = fabsf(t1) < 1.0e9f && fabsf(t2) < 1.0e9f;
   const int32_t f1 = __float2int_rd(t1), f2 = __float2int_rd(t2);
@@ -105,7 +104,6 @@ __device__ __forceinline__ bool pixel_fast(float brel1, float brel2, float inv_s
   key = ok ? (uint32_t)((iy + f2) * npix_x + (ix + f1)) : 0u;
   return ok;
 }
-
 // ---------------------------------------------------------------- brute force
 constexpr int BR_TX = 32;             // tile columns: one per lane
 constexpr int BR_TY = 64;             // tile rows: 64/R warps of R rows per thread

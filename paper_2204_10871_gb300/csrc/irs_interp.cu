@@ -460,16 +460,48 @@ struct IpRayArgs {
   X(8, 4, 16, 6, 4, 0) X(9, 8, 8, 8, 3, 0)
 constexpr int IP_NVARIANT = 10;
 
+// Row data of one pair of cell rows (2l, 2l + 1), read by the ray pass.
+struct __align__(16) IpRowPair {
+  float2 ty;    // tau_y h of both rows
+  float2 sgi;   // sigma_y = (l + 1/2) Q / k - v - 1/2 of both rows
+  float2 nsgi;  // -sigma_y
+  int32_t v0, v1;  // level-2 row offset v Q of both rows
+};
+
+// Dynamic shared memory of the ray pass (bytes, 16-byte aligned blocks):
+// near lenses as (-x, -x, -y, -y) and (-m, -m) pairs, the level-2 series
+// as conj duplicated (c.re, c.re, -c.im, -c.im), the row table and the
+// level-1 series.
+template <int Q, int K2>
+struct IpSmem {
+  static constexpr size_t near_xy = 0;
+  static constexpr size_t near_m = near_xy + sizeof(float4) * IP_NEAR_MAX;
+  static constexpr size_t sub = near_m + sizeof(float2) * IP_NEAR_MAX;
+  static constexpr size_t rows = sub + sizeof(float4) * Q * Q * K2;
+  static constexpr size_t coef = rows + sizeof(IpRowPair) * (IP_KMAX_RAYS / 2);
+  static constexpr size_t bytes = coef + sizeof(float2) * IP_KMAX;
+};
+
 // One level-1 cell: gather the 3x3 block's lenses, re-centre the series on the
 // sub-cells, then every ray of rows [jlo, jhi) of the cell.  In DUMP mode the
 // thread holding ray (want_i, want_j) writes its beta and pixel to slot `work`.
+//
+// Each thread takes one lattice column and R rows; rows go in pairs through
+// the packed FP32x2 instructions (two rows share the column's dx and sigma_x),
+// which round exactly as the scalar ones.  The accumulators hold -alpha (the
+// masses are stored negated) and the level-2 Horner runs on the conjugate, so
+// no negation is issued per ray.
 template <int MODE, int R, int Q, int K2, int BIN>
 __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpRayArgs& a, int64_t rc,
                                         int64_t want_i, int64_t want_j, int64_t work) {
-  __shared__ float4 near_s[IP_NEAR_MAX];
-  __shared__ float2 sub_s[Q * Q][K2];
-  __shared__ float4 row_s[IP_KMAX_RAYS];  // per cell row: t_y, sigma_y, level-2 row offset (bits)
-  __shared__ float2 c_s[IP_KMAX];
+  static_assert(R % 2 == 0, "rows go in pairs");
+  using L = IpSmem<Q, K2>;
+  extern __shared__ __align__(16) unsigned char ip_smem[];
+  float4* nxy_s = reinterpret_cast<float4*>(ip_smem + L::near_xy);
+  float2* nm_s = reinterpret_cast<float2*>(ip_smem + L::near_m);
+  float4* sub_s = reinterpret_cast<float4*>(ip_smem + L::sub);
+  IpRowPair* row_s = reinterpret_cast<IpRowPair*>(ip_smem + L::rows);
+  float2* c_s = reinterpret_cast<float2*>(ip_smem + L::coef);
   __shared__ CellRec rec_s;
   __shared__ int blk_start[9], blk_off[10];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -517,7 +549,9 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     while (q < 8 && t >= blk_off[q + 1]) ++q;
     const float4 v = a.rel[blk_start[q] + (t - blk_off[q])];
     const float ox = (float)((q % 3) - 1) * hf, oy = (float)((q / 3) - 1) * hf;
-    near_s[t] = make_float4(v.x + ox, v.y + oy, v.z, 0.f);
+    const float x = v.x + ox, y = v.y + oy;
+    nxy_s[t] = make_float4(-x, -x, -y, -y);
+    nm_s[t] = make_float2(-v.z, -v.z);
   }
   // level 2: re-centre the series on the sub-cell centres eps (cell units)
   for (int t = tid; t < Q * Q * K2; t += blockDim.x) {
@@ -537,99 +571,157 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
       ti = ni;
     }
     const float sc = powf((float)Q, -(float)nn);
-    sub_s[sub][nn] = make_float2(sr * sc, si * sc);
+    const float cr = sr * sc, ci = -(si * sc);
+    sub_s[t] = make_float4(cr, cr, ci, ci);
   }
-  // row table: t_y = tau_y h, sigma_y = (l + 1/2) Q / k - v - 1/2, v Q (level-2 row offset)
-  for (int l = tid; l < (int)(jhi - j0); l += blockDim.x) {
-    const float sv = ((float)l + 0.5f) * ((float)Q * inv_k);
-    const int v = min(__float2int_rd(sv), Q - 1);
-    row_s[l] = make_float4(fmaf((float)l, inv_k, 0.5f * inv_k - 0.5f) * hf, sv - (float)v - 0.5f,
-                           __int_as_float(v * Q), 0.f);
+  // row table: t_y = tau_y h, sigma_y = (l + 1/2) Q / k - v - 1/2, v Q, rows of
+  // the whole cell side in pairs (a last odd row's partner is never binned)
+  const int npair_cell = (int)((k + 1) >> 1);
+  for (int pr = tid; pr < npair_cell; pr += blockDim.x) {
+    IpRowPair rp;
+    float tyv[2], sg[2];
+    int vq[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int l = 2 * pr + j;
+      const float sv = ((float)l + 0.5f) * ((float)Q * inv_k);
+      const int v = min(__float2int_rd(sv), Q - 1);
+      tyv[j] = fmaf((float)l, inv_k, 0.5f * inv_k - 0.5f) * hf;
+      sg[j] = sv - (float)v - 0.5f;
+      vq[j] = v * Q;
+    }
+    rp.ty = make_float2(tyv[0], tyv[1]);
+    rp.sgi = make_float2(sg[0], sg[1]);
+    rp.nsgi = make_float2(-sg[0], -sg[1]);
+    rp.v0 = vq[0];
+    rp.v1 = vq[1];
+    row_s[pr] = rp;
   }
   __syncthreads();
 
   // base-pixel range of this cell for the 32-bit pixel test
   const int32_t lo1 = -rec_s.ix, hi1 = g.npix_x - rec_s.ix;
   const int32_t lo2 = -rec_s.iy, hi2 = g.npix_y - rec_s.iy;
-  const float bxh = rec_s.bx_hi, bxl = rec_s.bx_lo, byh = rec_s.by_hi, byl = rec_s.by_lo;
+  const float2 BXH = make_float2(rec_s.bx_hi, rec_s.bx_hi), BXL = make_float2(rec_s.bx_lo, rec_s.bx_lo);
+  const float2 BYH = make_float2(rec_s.by_hi, rec_s.by_hi), BYL = make_float2(rec_s.by_lo, rec_s.by_lo);
+  const float2 LAM1 = make_float2(g.lam_s1, g.lam_s1), LAM2 = make_float2(g.lam_s2, g.lam_s2);
+  const float2 ISX = make_float2(g.inv_sx, g.inv_sx), ISY = make_float2(g.inv_sy, g.inv_sy);
   const int n_corner = rec_s.n_corner;
   const int32_t rix = rec_s.ix, riy = rec_s.iy;
-  // cell-local 32-bit lattice indices: columns [0, kx), rows [ylo, yhi)
+  // cell-local 32-bit lattice indices: columns [0, kx), rows [ylo, yhi); units
+  // start on an even row so that row pairs line up with the table
   const int kx = (int)(i1 - i0), ylo = (int)(jlo - j0), yhi = (int)(jhi - j0);
+  const int ylo2 = ylo & ~1;
+  const int npair = (yhi + 1) >> 1;
   const float c_tau = 0.5f * inv_k - 0.5f;  // tau = (l + 1/2)/k - 1/2
   const float qk = (float)Q * inv_k;        // sub-cell index = floor((l + 1/2) Q / k)
   // work units (32-column strip x R-row group), dealt round-robin to warps
   const int nwarps = blockDim.x / 32;
   const int nstrip = (kx + 31) / 32;
-  const int nrg = (yhi - ylo + R - 1) / R;
+  const int nrg = (yhi - ylo2 + R - 1) / R;
   const int nunit = nstrip * nrg;
   for (int unit = warp; unit < nunit; unit += nwarps) {
     const int st = unit % nstrip, rg = unit / nstrip;
     const int cl = st * 32 + lane;
-    const int rl0 = ylo + rg * R;
-    const float taux = fmaf((float)cl, inv_k, c_tau);
-    const float tx = taux * hf;
+    const int rl0 = ylo2 + rg * R;
+    const int p0 = rl0 >> 1;
+    const float tx = fmaf((float)cl, inv_k, c_tau) * hf;
     const float su = ((float)cl + 0.5f) * qk;
     const int u = min(__float2int_rd(su), Q - 1);
     const float sgr = su - (float)u - 0.5f;
-    float ty[R], ax[R], ay[R];
+    const float2 TX = make_float2(tx, tx), SGR = make_float2(sgr, sgr);
+    float2 TY[R / 2], NAX[R / 2], NAY[R / 2];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      ty[r] = row_s[min(rl0 + r, yhi - 1)].x;  // rows past the cell end are masked later
-      ax[r] = ay[r] = 0.f;
+    for (int i = 0; i < R / 2; ++i) {
+      TY[i] = row_s[min(p0 + i, npair - 1)].ty;  // rows past the cell end are masked later
+      NAX[i] = NAY[i] = make_float2(0.f, 0.f);
     }
 #pragma unroll 2
     for (int q = 0; q < n_near; ++q) {
-      const float4 L = near_s[q];
-      const float dx = tx - L.x;
-      const float dx2 = dx * dx;
+      const float4 Lq = nxy_s[q];
+      const float2 NM = nm_s[q];
+      const float2 DX = __fadd2_rn(TX, make_float2(Lq.x, Lq.y));
+      const float2 DX2 = __fmul2_rn(DX, DX);
+      const float2 NLY = make_float2(Lq.z, Lq.w);
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float dy = ty[r] - L.y;
-        const float r2 = fmaf(dy, dy, dx2);
-        const float w = L.z * rcp_approx(r2);
-        ax[r] = fmaf(w, dx, ax[r]);
-        ay[r] = fmaf(w, dy, ay[r]);
+      for (int i = 0; i < R / 2; ++i) {
+        const float2 DY = __fadd2_rn(TY[i], NLY);
+        const float2 R2 = __ffma2_rn(DY, DY, DX2);
+        const float2 W = __fmul2_rn(NM, make_float2(rcp_approx(R2.x), rcp_approx(R2.y)));
+        NAX[i] = __ffma2_rn(W, DX, NAX[i]);
+        NAY[i] = __ffma2_rn(W, DY, NAY[i]);
       }
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int rl = rl0 + r;
-      const bool inside = cl < kx && rl < yhi;
-      // sub-cell and its series in sigma = (tau - eps) Q = (l + 1/2) Q / k - v - 1/2
-      const float4 rw = row_s[min(rl, yhi - 1)];
-      const float sgi = rw.y;
-      const float2* d = sub_s[__float_as_int(rw.z) + u];
-      float pr = d[K2 - 1].x, pi = d[K2 - 1].y;
+    for (int i = 0; i < R / 2; ++i) {
+      const IpRowPair rp = row_s[min(p0 + i, npair - 1)];
+      // conj of the level-2 series in sigma, both rows at once
+      float2 QR, QI;
+      if (rp.v0 == rp.v1) {  // both rows in one sub-cell row: uniform over the warp
+        const float4* d = sub_s + (rp.v0 + u) * K2;
+        const float4 dl = d[K2 - 1];
+        QR = make_float2(dl.x, dl.y);
+        QI = make_float2(dl.z, dl.w);
 #pragma unroll
-      for (int nn = K2 - 2; nn >= 0; --nn) {
-        const float2 dn = d[nn];
-        const float nr = fmaf(pr, sgr, fmaf(-pi, sgi, dn.x));
-        const float ni = fmaf(pr, sgi, fmaf(pi, sgr, dn.y));
-        pr = nr;
-        pi = ni;
-      }
-      if (n_corner) {
-        for (int q = 0; q < n_corner; ++q) {
-          const float wr = rec_s.corner[q][0] + tx, wi = rec_s.corner[q][1] + ty[r];
-          const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
-          const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
-          pr += rec_s.corner[q][2] * pli;
-          pi -= rec_s.corner[q][2] * plr;
+        for (int nn = K2 - 2; nn >= 0; --nn) {
+          const float4 dn = d[nn];
+          const float2 t1 = __ffma2_rn(QI, rp.sgi, make_float2(dn.x, dn.y));
+          const float2 t2 = __ffma2_rn(QI, SGR, make_float2(dn.z, dn.w));
+          const float2 nr = __ffma2_rn(QR, SGR, t1);
+          QI = __ffma2_rn(QR, rp.nsgi, t2);
+          QR = nr;
+        }
+      } else {
+        const float4* da = sub_s + (rp.v0 + u) * K2;
+        const float4* db = sub_s + (rp.v1 + u) * K2;
+        QR = make_float2(da[K2 - 1].x, db[K2 - 1].x);
+        QI = make_float2(da[K2 - 1].z, db[K2 - 1].z);
+#pragma unroll
+        for (int nn = K2 - 2; nn >= 0; --nn) {
+          const float4 ea = da[nn], eb = db[nn];
+          const float2 t1 = __ffma2_rn(QI, rp.sgi, make_float2(ea.x, eb.x));
+          const float2 t2 = __ffma2_rn(QI, SGR, make_float2(ea.z, eb.z));
+          const float2 nr = __ffma2_rn(QR, SGR, t1);
+          QI = __ffma2_rn(QR, rp.nsgi, t2);
+          QR = nr;
         }
       }
-      const float b1 = bxh + ((bxl - ax[r]) + (g.lam_s1 * tx + pr));
-      const float b2 = byh + ((byl - ay[r]) + (g.lam_s2 * ty[r] - pi));
-      uint32_t key;
-      const bool ok =
-          pixel_fast(b1, b2, g.inv_sx, g.inv_sy, lo1, hi1, lo2, hi2, rix, riy, g.npix_x, key) && inside;
-      if (MODE == IP_MAP) {
-        if (BIN) bin_warp_runs(a.counts, ok, key);
-        else bin_warp(a.counts, ok, key);
-      } else if (i0 + cl == want_i && j0 + rl == want_j) {
-        a.beta_out[2 * work] = (g.src_x0 + (double)rix * g.sx) + (double)b1;
-        a.beta_out[2 * work + 1] = (g.src_y0 + (double)riy * g.sy) + (double)b2;
-        if (a.pix_out) a.pix_out[work] = ok ? (int64_t)key : -1;
+      if (n_corner) {  // corners of the sheet near this cell, per ray
+        float qr[2] = {QR.x, QR.y}, qi[2] = {QI.x, QI.y};
+        const float tyr[2] = {rp.ty.x, rp.ty.y};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          for (int c = 0; c < n_corner; ++c) {
+            const float wr = rec_s.corner[c][0] + tx, wi = rec_s.corner[c][1] + tyr[j];
+            const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
+            const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
+            qr[j] += rec_s.corner[c][2] * pli;
+            qi[j] += rec_s.corner[c][2] * plr;
+          }
+        }
+        QR = make_float2(qr[0], qr[1]);
+        QI = make_float2(qi[0], qi[1]);
+      }
+      // beta relative to the base pixel: centre + lambda tau h + L_local - alpha_near
+      const float2 B1 = __fadd2_rn(BXH, __fadd2_rn(__fadd2_rn(BXL, NAX[i]), __ffma2_rn(LAM1, TX, QR)));
+      const float2 B2 = __fadd2_rn(BYH, __fadd2_rn(__fadd2_rn(BYL, NAY[i]), __ffma2_rn(LAM2, rp.ty, QI)));
+      const float2 T1 = __fmul2_rn(B1, ISX), T2 = __fmul2_rn(B2, ISY);
+      const float t1[2] = {T1.x, T1.y}, t2[2] = {T2.x, T2.y};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int rl = rl0 + 2 * i + j;
+        const bool inside = cl < kx && rl >= ylo && rl < yhi;
+        uint32_t key;
+        const bool ok = pixel_scaled(t1[j], t2[j], lo1, hi1, lo2, hi2, rix, riy, g.npix_x, key) && inside;
+        if (MODE == IP_MAP) {
+          if (BIN) bin_warp_runs(a.counts, ok, key);
+          else bin_warp(a.counts, ok, key);
+        } else if (i0 + cl == want_i && j0 + rl == want_j) {
+          const float b1 = j ? B1.y : B1.x, b2 = j ? B2.y : B2.x;
+          a.beta_out[2 * work] = (g.src_x0 + (double)rix * g.sx) + (double)b1;
+          a.beta_out[2 * work + 1] = (g.src_y0 + (double)riy * g.sy) + (double)b2;
+          if (a.pix_out) a.pix_out[work] = ok ? (int64_t)key : -1;
+        }
       }
     }
   }
@@ -697,10 +789,31 @@ k_ip_ray_batch(const MapDesc* __restrict__ maps, int nmaps, int64_t nitems,
   }
 }
 
+// Dynamic shared memory above the 48 KB default: set once per instantiation,
+// before any launch or graph capture that uses it.
+#define IP_DECL_ATTR(V, R, Q, K2, MINB, BIN)                                                           \
+  case V: {                                                                                            \
+    const int b = (int)IpSmem<Q, K2>::bytes;                                                          \
+    e = cudaFuncSetAttribute(k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN>,                                   \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);                         \
+    if (e == cudaSuccess)                                                                              \
+      e = cudaFuncSetAttribute(k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN>,                                \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, b);                       \
+    if (e == cudaSuccess)                                                                              \
+      e = cudaFuncSetAttribute(k_ip_ray_batch<R, Q, K2, MINB, BIN>,                                   \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, b);                       \
+    break;                                                                                             \
+  }
+cudaError_t ip_ray_attributes(int variant) {
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (variant) { IP_VARIANTS(IP_DECL_ATTR) default: break; }
+  return e;
+}
+
 #define IP_DECL_OCC(V, R, Q, K2, MINB, BIN)                                                       \
   case V:                                                                                         \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN>, \
-                                                  IP_THREADS, 0);                                 \
+                                                  IP_THREADS, IpSmem<Q, K2>::bytes);              \
     break;
 int ip_ray_occupancy(int variant) {
   int per_sm = 0;
@@ -708,12 +821,14 @@ int ip_ray_occupancy(int variant) {
   return per_sm > 0 ? per_sm : 1;
 }
 
-#define IP_DECL_LAUNCH(V, R, Q, K2, MINB, BIN)                                                \
-  case V:                                                                                     \
-    if (mode == IP_MAP)                                                                       \
-      k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, 0, s>>>(g, ig, a);  \
-    else                                                                                      \
-      k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, 0, s>>>(g, ig, a); \
+#define IP_DECL_LAUNCH(V, R, Q, K2, MINB, BIN)                                                           \
+  case V:                                                                                                \
+    if (mode == IP_MAP)                                                                                  \
+      k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(g, ig, \
+                                                                                                   a);   \
+    else                                                                                                 \
+      k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(g,    \
+                                                                                                 ig, a); \
     break;
 cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, const Geo& g,
                           const IpGeo& ig, const IpRayArgs& a) {
@@ -721,10 +836,10 @@ cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, c
   return cudaGetLastError();
 }
 
-#define IP_DECL_BATCH(V, R, Q, K2, MINB, BIN)                                                \
-  case V:                                                                                    \
-    k_ip_ray_batch<R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, 0, s>>>(maps, nmaps,       \
-                                                                             nitems, queue); \
+#define IP_DECL_BATCH(V, R, Q, K2, MINB, BIN)                                                       \
+  case V:                                                                                           \
+    k_ip_ray_batch<R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(   \
+        maps, nmaps, nitems, queue);                                                                \
     break;
 cudaError_t launch_ip_ray_batch(int variant, int64_t grid, cudaStream_t s, const MapDesc* maps,
                                 int nmaps, int64_t nitems, unsigned long long* queue) {
@@ -944,6 +1059,7 @@ irs_status interp_plan(irs_plan_t* P) {
   if (cudaGetLastError() != cudaSuccess) return IRS_ERR_CUDA;
   if (fft2d_forward(S->kspec, f.Nx, f.Ny, G, S->kspec, f, nker, 0) != cudaSuccess) return IRS_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return IRS_ERR_CUDA;
+  if (ip_ray_attributes(ig.variant) != cudaSuccess) return IRS_ERR_CUDA;
   S->grid_ray = P->num_sms * ip_ray_occupancy(ig.variant);
   if (p.method == IRS_MLP) {
     if (p.plane != IRS_PLANE_RECT) return IRS_ERR_UNSUPPORTED;
