@@ -60,16 +60,21 @@ __device__ __forceinline__ void bin_warp(uint32_t* counts, bool valid, uint32_t 
   if (valid && lane == __ffs(peers) - 1) atomicAdd(counts + key, (uint32_t)__popc(peers));
 }
 
+// Key forms (~0u = no pixel) for the ray pass.  The leader of each group of
+// equal keys is its lowest lane: no lower lane (lane_lt = its lane mask) shares it.
+__device__ __forceinline__ void bin_warp_key(uint32_t* counts, uint32_t key, unsigned lane_lt) {
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+  if (key != 0xFFFFFFFFu && (peers & lane_lt) == 0u) atomicAdd(counts + key, (uint32_t)__popc(peers));
+}
+
 // Run-length variant: lanes hold consecutive columns of one row, so equal
-// pixels usually come in runs; the first lane of each run of equal valid keys
-// adds the run's length (non-adjacent equal keys add separately).
-__device__ __forceinline__ void bin_warp_runs(uint32_t* counts, bool valid, uint32_t key) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t k = valid ? key : 0xFFFFFFFFu;
-  const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, k, 1);
-  const bool head = (lane == 0) || (k != prev);
+// pixels usually come in runs; the first lane of each run of equal keys adds
+// the run's length (non-adjacent equal keys add separately).
+__device__ __forceinline__ void bin_warp_runs_key(uint32_t* counts, uint32_t key, int lane) {
+  const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+  const bool head = (lane == 0) || (key != prev);
   const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
-  if (valid && head) {
+  if (key != 0xFFFFFFFFu && head) {
     const unsigned later = heads & ~((2u << lane) - 1u);  // heads after this lane
     const int next = later ? __ffs(later) - 1 : 32;
     atomicAdd(counts + key, (uint32_t)(next - lane));
@@ -77,7 +82,8 @@ __device__ __forceinline__ void bin_warp_runs(uint32_t* counts, bool valid, uint
 }
 
 // Pixel of a ray from its position relative to the base pixel's lower-left
-// corner (brel1, brel2 in theta_E) -- reading R7, floor per axis.
+// corner (brel1, brel2 in theta_E): floor per axis, so a ray on a pixel edge
+// belongs to the pixel above / to the right of it.
 __device__ __forceinline__ bool pixel_from_rel(const Geo& g, int32_t ix, int32_t iy, float brel1,
                                                float brel2, uint32_t& key, int64_t& pix) {
   pix = -1;
@@ -91,19 +97,20 @@ __device__ __forceinline__ bool pixel_from_rel(const Geo& g, int32_t ix, int32_t
   return true;
 }
 
-// Pixel of a ray in 32-bit arithmetic from its offset to the base pixel in
-// pixel units (t = beta_rel / s): NaN, Inf and far-off rays fail the finiteness
-// test, the rest are floored and range-tested against the cell's base pixel
-// (lo = -base, hi = npix - base).
-__device__ __forceinline__ bool pixel_scaled(float t1, float t2, int32_t lo1, int32_t hi1, int32_t lo2,
-                                             int32_t hi2, int32_t ix, int32_t iy, int32_t npix_x, uint32_t& key) {
-  // finite and within int range (NaN fails both compares); then one round-down each
-  const bool fin = fabsf(t1) < 1.0e9f && fabsf(t2) < 1.0e9f;
-  const int32_t f1 = __float2int_rd(t1), f2 = __float2int_rd(t2);
-  const bool ok = fin && (f1 >= lo1) && (f1 < hi1) && (f2 >= lo2) && (f2 < hi2);
-  key = ok ? (uint32_t)((iy + f2) * npix_x + (ix + f1)) : 0u;
-  return ok;
+// Pixel key of a ray from its offset to the cell's base pixel (ix, iy) in
+// pixel units (t = beta_rel / s), floor per axis as in pixel_from_rel; ~0u if
+// the ray misses the map.  NaN rays fail the ordered test; +-Inf and huge
+// offsets saturate the conversion and, with |ix|, |iy| <= 1e9, cannot wrap
+// (mod 2^32) into range.
+__device__ __forceinline__ uint32_t pixel_key(float t1, float t2, int32_t ix, int32_t iy, int32_t npix_x,
+                                              int32_t npix_y) {
+  const bool num = !isnan(t1) && !isnan(t2);
+  const uint32_t px = (uint32_t)ix + (uint32_t)__float2int_rd(t1);
+  const uint32_t py = (uint32_t)iy + (uint32_t)__float2int_rd(t2);
+  const bool ok = num && px < (uint32_t)npix_x && py < (uint32_t)npix_y;
+  return ok ? py * (uint32_t)npix_x + px : 0xFFFFFFFFu;
 }
+
 // ---------------------------------------------------------------- brute force
 constexpr int BR_TX = 32;             // tile columns: one per lane
 constexpr int BR_TY = 64;             // tile rows: 64/R warps of R rows per thread

@@ -462,9 +462,9 @@ constexpr int IP_NVARIANT = 10;
 
 // Row data of one pair of cell rows (2l, 2l + 1), read by the ray pass.
 struct __align__(16) IpRowPair {
-  float2 ty;    // tau_y h of both rows
   float2 sgi;   // sigma_y = (l + 1/2) Q / k - v - 1/2 of both rows
   float2 nsgi;  // -sigma_y
+  float2 ty;    // tau_y h of both rows
   int32_t v0, v1;  // level-2 row offset v Q of both rows
 };
 
@@ -599,15 +599,10 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   }
   __syncthreads();
 
-  // base-pixel range of this cell for the 32-bit pixel test
-  const int32_t lo1 = -rec_s.ix, hi1 = g.npix_x - rec_s.ix;
-  const int32_t lo2 = -rec_s.iy, hi2 = g.npix_y - rec_s.iy;
-  const float2 BXH = make_float2(rec_s.bx_hi, rec_s.bx_hi), BXL = make_float2(rec_s.bx_lo, rec_s.bx_lo);
-  const float2 BYH = make_float2(rec_s.by_hi, rec_s.by_hi), BYL = make_float2(rec_s.by_lo, rec_s.by_lo);
-  const float2 LAM1 = make_float2(g.lam_s1, g.lam_s1), LAM2 = make_float2(g.lam_s2, g.lam_s2);
-  const float2 ISX = make_float2(g.inv_sx, g.inv_sx), ISY = make_float2(g.inv_sy, g.inv_sy);
-  const int n_corner = rec_s.n_corner;
+  // base pixel of this cell for the 32-bit pixel test
   const int32_t rix = rec_s.ix, riy = rec_s.iy;
+  const int n_corner = rec_s.n_corner;
+  const unsigned lane_lt = (1u << lane) - 1u;
   // cell-local 32-bit lattice indices: columns [0, kx), rows [ylo, yhi); units
   // start on an even row so that row pairs line up with the table
   const int kx = (int)(i1 - i0), ylo = (int)(jlo - j0), yhi = (int)(jhi - j0);
@@ -615,6 +610,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   const int npair = (yhi + 1) >> 1;
   const float c_tau = 0.5f * inv_k - 0.5f;  // tau = (l + 1/2)/k - 1/2
   const float qk = (float)Q * inv_k;        // sub-cell index = floor((l + 1/2) Q / k)
+  const float fnan = __int_as_float(0x7fffffff);
   // work units (32-column strip x R-row group), dealt round-robin to warps
   const int nwarps = blockDim.x / 32;
   const int nstrip = (kx + 31) / 32;
@@ -625,16 +621,21 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     const int cl = st * 32 + lane;
     const int rl0 = ylo2 + rg * R;
     const int p0 = rl0 >> 1;
-    const float tx = fmaf((float)cl, inv_k, c_tau) * hf;
     const float su = ((float)cl + 0.5f) * qk;
     const int u = min(__float2int_rd(su), Q - 1);
     const float sgr = su - (float)u - 0.5f;
+    // rays outside the cell's columns get a NaN x, rays outside its rows a NaN
+    // y accumulator: both reach beta whatever the near sum does and fail the
+    // pixel test
+    const float tx = cl < kx ? fmaf((float)cl, inv_k, c_tau) * hf : fnan;
     const float2 TX = make_float2(tx, tx), SGR = make_float2(sgr, sgr);
     float2 TY[R / 2], NAX[R / 2], NAY[R / 2];
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
-      TY[i] = row_s[min(p0 + i, npair - 1)].ty;  // rows past the cell end are masked later
-      NAX[i] = NAY[i] = make_float2(0.f, 0.f);
+      TY[i] = row_s[min(p0 + i, npair - 1)].ty;
+      const int ra = rl0 + 2 * i;
+      NAX[i] = make_float2(0.f, 0.f);
+      NAY[i] = make_float2(ra >= ylo && ra < yhi ? 0.f : fnan, ra + 1 < yhi ? 0.f : fnan);
     }
 #pragma unroll 2
     for (int q = 0; q < n_near; ++q) {
@@ -652,75 +653,127 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
         NAY[i] = __ffma2_rn(W, DY, NAY[i]);
       }
     }
+    // tail in groups of HP row pairs: level-2 series (conj, in sigma), sheet
+    // corners, beta and pixel keys, binning; the chains of a group interleave
+    constexpr int HP = R / 2 < 2 ? R / 2 : 2;
 #pragma unroll
-    for (int i = 0; i < R / 2; ++i) {
-      const IpRowPair rp = row_s[min(p0 + i, npair - 1)];
-      // conj of the level-2 series in sigma, both rows at once
-      float2 QR, QI;
-      if (rp.v0 == rp.v1) {  // both rows in one sub-cell row: uniform over the warp
-        const float4* d = sub_s + (rp.v0 + u) * K2;
-        const float4 dl = d[K2 - 1];
-        QR = make_float2(dl.x, dl.y);
-        QI = make_float2(dl.z, dl.w);
+    for (int h = 0; h < R / 2; h += HP) {
+      float2 QR[HP], QI[HP];
+      {
+        float4 SG[HP];  // (sigma_y, -sigma_y) of the pair
+        int va[HP];
+        bool aligned = true;  // no pair straddles a sub-cell row: uniform over the warp
 #pragma unroll
-        for (int nn = K2 - 2; nn >= 0; --nn) {
-          const float4 dn = d[nn];
-          const float2 t1 = __ffma2_rn(QI, rp.sgi, make_float2(dn.x, dn.y));
-          const float2 t2 = __ffma2_rn(QI, SGR, make_float2(dn.z, dn.w));
-          const float2 nr = __ffma2_rn(QR, SGR, t1);
-          QI = __ffma2_rn(QR, rp.nsgi, t2);
-          QR = nr;
+        for (int i = 0; i < HP; ++i) {
+          const IpRowPair* rp = row_s + min(p0 + h + i, npair - 1);
+          SG[i] = *reinterpret_cast<const float4*>(rp);
+          const int2 v = *reinterpret_cast<const int2*>(&rp->v0);
+          va[i] = (v.x + u) * K2;
+          aligned = aligned && (v.x == v.y);
         }
-      } else {
-        const float4* da = sub_s + (rp.v0 + u) * K2;
-        const float4* db = sub_s + (rp.v1 + u) * K2;
-        QR = make_float2(da[K2 - 1].x, db[K2 - 1].x);
-        QI = make_float2(da[K2 - 1].z, db[K2 - 1].z);
+        if (aligned) {
 #pragma unroll
-        for (int nn = K2 - 2; nn >= 0; --nn) {
-          const float4 ea = da[nn], eb = db[nn];
-          const float2 t1 = __ffma2_rn(QI, rp.sgi, make_float2(ea.x, eb.x));
-          const float2 t2 = __ffma2_rn(QI, SGR, make_float2(ea.z, eb.z));
-          const float2 nr = __ffma2_rn(QR, SGR, t1);
-          QI = __ffma2_rn(QR, rp.nsgi, t2);
-          QR = nr;
-        }
-      }
-      if (n_corner) {  // corners of the sheet near this cell, per ray
-        float qr[2] = {QR.x, QR.y}, qi[2] = {QI.x, QI.y};
-        const float tyr[2] = {rp.ty.x, rp.ty.y};
+          for (int i = 0; i < HP; ++i) {
+            const float4 dl = sub_s[va[i] + K2 - 1];
+            QR[i] = make_float2(dl.x, dl.y);
+            QI[i] = make_float2(dl.z, dl.w);
+          }
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          for (int c = 0; c < n_corner; ++c) {
-            const float wr = rec_s.corner[c][0] + tx, wi = rec_s.corner[c][1] + tyr[j];
-            const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
-            const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
-            qr[j] += rec_s.corner[c][2] * pli;
-            qi[j] += rec_s.corner[c][2] * plr;
+          for (int nn = K2 - 2; nn >= 0; --nn) {
+#pragma unroll
+            for (int i = 0; i < HP; ++i) {
+              const float4 dn = sub_s[va[i] + nn];
+              const float2 sgi = make_float2(SG[i].x, SG[i].y), nsgi = make_float2(SG[i].z, SG[i].w);
+              const float2 t1 = __ffma2_rn(QI[i], sgi, make_float2(dn.x, dn.y));
+              const float2 t2 = __ffma2_rn(QI[i], SGR, make_float2(dn.z, dn.w));
+              const float2 nr = __ffma2_rn(QR[i], SGR, t1);
+              QI[i] = __ffma2_rn(QR[i], nsgi, t2);
+              QR[i] = nr;
+            }
+          }
+        } else {
+          int vb[HP];
+#pragma unroll
+          for (int i = 0; i < HP; ++i) vb[i] = (row_s[min(p0 + h + i, npair - 1)].v1 + u) * K2;
+#pragma unroll
+          for (int i = 0; i < HP; ++i) {
+            const float4 ea = sub_s[va[i] + K2 - 1], eb = sub_s[vb[i] + K2 - 1];
+            QR[i] = make_float2(ea.x, eb.x);
+            QI[i] = make_float2(ea.z, eb.z);
+          }
+#pragma unroll
+          for (int nn = K2 - 2; nn >= 0; --nn) {
+#pragma unroll
+            for (int i = 0; i < HP; ++i) {
+              const float4 ea = sub_s[va[i] + nn], eb = sub_s[vb[i] + nn];
+              const float2 sgi = make_float2(SG[i].x, SG[i].y), nsgi = make_float2(SG[i].z, SG[i].w);
+              const float2 t1 = __ffma2_rn(QI[i], sgi, make_float2(ea.x, eb.x));
+              const float2 t2 = __ffma2_rn(QI[i], SGR, make_float2(ea.z, eb.z));
+              const float2 nr = __ffma2_rn(QR[i], SGR, t1);
+              QI[i] = __ffma2_rn(QR[i], nsgi, t2);
+              QR[i] = nr;
+            }
           }
         }
-        QR = make_float2(qr[0], qr[1]);
-        QI = make_float2(qi[0], qi[1]);
       }
-      // beta relative to the base pixel: centre + lambda tau h + L_local - alpha_near
-      const float2 B1 = __fadd2_rn(BXH, __fadd2_rn(__fadd2_rn(BXL, NAX[i]), __ffma2_rn(LAM1, TX, QR)));
-      const float2 B2 = __fadd2_rn(BYH, __fadd2_rn(__fadd2_rn(BYL, NAY[i]), __ffma2_rn(LAM2, rp.ty, QI)));
-      const float2 T1 = __fmul2_rn(B1, ISX), T2 = __fmul2_rn(B2, ISY);
-      const float t1[2] = {T1.x, T1.y}, t2[2] = {T2.x, T2.y};
+      if (n_corner) {  // corners of the sheet near this cell, per ray (uniform over the CTA)
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int rl = rl0 + 2 * i + j;
-        const bool inside = cl < kx && rl >= ylo && rl < yhi;
-        uint32_t key;
-        const bool ok = pixel_scaled(t1[j], t2[j], lo1, hi1, lo2, hi2, rix, riy, g.npix_x, key) && inside;
-        if (MODE == IP_MAP) {
-          if (BIN) bin_warp_runs(a.counts, ok, key);
-          else bin_warp(a.counts, ok, key);
-        } else if (i0 + cl == want_i && j0 + rl == want_j) {
-          const float b1 = j ? B1.y : B1.x, b2 = j ? B2.y : B2.x;
-          a.beta_out[2 * work] = (g.src_x0 + (double)rix * g.sx) + (double)b1;
-          a.beta_out[2 * work + 1] = (g.src_y0 + (double)riy * g.sy) + (double)b2;
-          if (a.pix_out) a.pix_out[work] = ok ? (int64_t)key : -1;
+        for (int i = 0; i < HP; ++i) {
+          float qr[2] = {QR[i].x, QR[i].y}, qi[2] = {QI[i].x, QI[i].y};
+          const float2 ty = row_s[min(p0 + h + i, npair - 1)].ty;
+          const float tyr[2] = {ty.x, ty.y};
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            for (int c = 0; c < n_corner; ++c) {
+              const float wr = rec_s.corner[c][0] + tx, wi = rec_s.corner[c][1] + tyr[j];
+              const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
+              const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
+              qr[j] += rec_s.corner[c][2] * pli;
+              qi[j] += rec_s.corner[c][2] * plr;
+            }
+          }
+          QR[i] = make_float2(qr[0], qr[1]);
+          QI[i] = make_float2(qi[0], qi[1]);
+        }
+      }
+      // beta relative to the base pixel (centre + lambda tau h + L_local -
+      // alpha_near) in pixel units, then the pixel key of every ray (~0 where
+      // none)
+      uint32_t key[2 * HP];
+#pragma unroll
+      for (int i = 0; i < HP; ++i) {
+        const float2 ty = row_s[min(p0 + h + i, npair - 1)].ty;
+        const float4 cx4 = make_float4(rec_s.bx_hi, rec_s.bx_hi, rec_s.bx_lo, rec_s.bx_lo);
+        const float4 cy4 = make_float4(rec_s.by_hi, rec_s.by_hi, rec_s.by_lo, rec_s.by_lo);
+        const float4 lm4 = make_float4(g.lam_s1, g.lam_s1, g.lam_s2, g.lam_s2);
+        const float4 is4 = make_float4(g.inv_sx, g.inv_sx, g.inv_sy, g.inv_sy);
+        const float2 B1 = __fadd2_rn(make_float2(cx4.x, cx4.y),
+                                     __fadd2_rn(__fadd2_rn(make_float2(cx4.z, cx4.w), NAX[h + i]),
+                                                __ffma2_rn(make_float2(lm4.x, lm4.y), TX, QR[i])));
+        const float2 B2 = __fadd2_rn(make_float2(cy4.x, cy4.y),
+                                     __fadd2_rn(__fadd2_rn(make_float2(cy4.z, cy4.w), NAY[h + i]),
+                                                __ffma2_rn(make_float2(lm4.z, lm4.w), ty, QI[i])));
+        const float2 T1 = __fmul2_rn(B1, make_float2(is4.x, is4.y));
+        const float2 T2 = __fmul2_rn(B2, make_float2(is4.z, is4.w));
+        key[2 * i] = pixel_key(T1.x, T2.x, rix, riy, g.npix_x, g.npix_y);
+        key[2 * i + 1] = pixel_key(T1.y, T2.y, rix, riy, g.npix_x, g.npix_y);
+        if (MODE == IP_DUMP) {
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            if (i0 + cl == want_i && j0 + rl0 + 2 * (h + i) + j == want_j) {
+              const float b1 = j ? B1.y : B1.x, b2 = j ? B2.y : B2.x;
+              a.beta_out[2 * work] = (g.src_x0 + (double)rix * g.sx) + (double)b1;
+              a.beta_out[2 * work + 1] = (g.src_y0 + (double)riy * g.sy) + (double)b2;
+              if (a.pix_out) a.pix_out[work] = key[2 * i + j] != 0xFFFFFFFFu ? (int64_t)key[2 * i + j] : -1;
+            }
+          }
+        }
+      }
+      if (MODE == IP_MAP) {
+#pragma unroll
+        for (int r = 0; r < 2 * HP; ++r) {
+          if (BIN) bin_warp_runs_key(a.counts, key[r], lane);
+          else bin_warp_key(a.counts, key[r], lane_lt);
         }
       }
     }
