@@ -150,10 +150,22 @@ def lens_field(lensgen, box, seed, w=WORKLOAD):
 
 # ------------------------------------------------------------------ ours
 # Per-ray work of the interpolated ray pass, in flops: 10 per near pair (the
-# same pair arithmetic as the brute force), 8 per complex Horner term of the
-# level-2 series (10 terms), and 20 for the smooth terms, sub-cell index and pixel.
-IP_SUB_TERMS = 10
-IP_FLOPS_FIXED = 8 * IP_SUB_TERMS + 20
+# same pair arithmetic as the brute force), 8 per complex multiply-add of the
+# level-2 Horner (K2 - 1 of them for K2 series terms), and 20 for the smooth
+# terms, sub-cell index and pixel.
+IP_VARIANT_K2 = [8, 6, 6, 6, 6, 6, 6, 6, 6, 8]  # series terms K2 of ray-pass variants 0..9
+IP_FLOPS_OTHER = 20
+
+
+def ip_flops_fixed(variant):
+    return 8 * (IP_VARIANT_K2[variant] - 1) + IP_FLOPS_OTHER
+
+
+# DRAM bytes per launch of the ray pass (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only for the kernel build, workload and cell
+# size they were captured on: (workload, cell multiplier, variant) -> bytes.
+# Source: profiles/k_ip_ray_paper-mid-full.md.
+IP_TRAFFIC = {("paper-mid", 1.0, 7): 46.848768e6 + 11.264e3}
 
 
 def mean_near_lenses(info, xy):
@@ -303,17 +315,22 @@ def run_ours(args):
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     peak_tflops = n_sms * 128 * 2 * sm_max * 1e6 / 1e12
     ray_ms_mean = float(np.mean(ray_ms))
+    traffic = None
     if full:
         n_near = mean_near_lenses(info, xy)
-        flops_per_ray = 10.0 * n_near + IP_FLOPS_FIXED
-        kname = "k_ip_ray (near pair sum + level-2 Horner, FP32 pipe + MUFU)"
+        variant = int(params.kernel_variant)
+        flops_per_ray = 10.0 * n_near + ip_flops_fixed(variant)
+        kname = f"k_ip_ray variant {variant} (near pair sum + level-2 Horner, FP32 pipe + MUFU)"
+        key = (w["name"].split(":")[0], round(float(params.cell_mult or 1.0), 2), variant)
+        if key in IP_TRAFFIC:
+            traffic = IP_TRAFFIC[key]
     else:
         n_near = None
         flops_per_ray = 10.0 * w["n_star"]
         kname = "k_brute (pair sum, FP32 pipe + MUFU)"
     achieved = flops_per_ray * rays_per_step / (ray_ms_mean * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                 "peak_basis": f"{n_sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
                               "(max SM clock of MEASURED_PEAKS.json)",
                 "flops_per_ray": flops_per_ray}

@@ -453,11 +453,15 @@ struct IpRayArgs {
 // nearest far lens's field (sub-cell half-diagonal / distance to it: 0.083
 // and 0.042).
 // MINB: CTAs per SM the register budget is sized for; BIN: warp binning by
-// __match_any_sync (0) or by runs of equal pixels (1).
+// __match_any_sync (0) or by runs of equal pixels (1); NPR: how many of a
+// thread's R/2 row pairs share one reciprocal per lens, 1/(r_a^2 r_b^2) (the
+// near sum is bound by the MUFU's 16 reciprocals per SM per clock; a shared
+// reciprocal trades one MUFU op for FP32 work on a pipe that is half idle).
 #define IP_VARIANTS(X)                                                                       \
-  X(0, 8, 8, 8, 2, 0) X(1, 8, 16, 6, 2, 0) X(2, 4, 8, 8, 2, 0) X(3, 4, 16, 6, 2, 0)           \
-  X(4, 8, 16, 6, 2, 1) X(5, 8, 16, 6, 3, 1) X(6, 4, 16, 6, 3, 1) X(7, 8, 16, 6, 3, 0)           \
-  X(8, 4, 16, 6, 4, 0) X(9, 8, 8, 8, 3, 0)
+  X(0, 8, 8, 8, 2, 0, 0) X(1, 8, 16, 6, 2, 0, 0) X(2, 8, 16, 6, 3, 0, 2)                       \
+  X(3, 8, 16, 6, 3, 0, 4) X(4, 8, 16, 6, 2, 1, 0) X(5, 8, 16, 6, 3, 1, 0)                      \
+  X(6, 8, 16, 6, 3, 1, 2) X(7, 8, 16, 6, 3, 0, 0) X(8, 4, 16, 6, 4, 0, 0)                      \
+  X(9, 8, 8, 8, 3, 0, 0)
 constexpr int IP_NVARIANT = 10;
 
 // Row data of one pair of cell rows (2l, 2l + 1), read by the ray pass.
@@ -491,10 +495,11 @@ struct IpSmem {
 // which round exactly as the scalar ones.  The accumulators hold -alpha (the
 // masses are stored negated) and the level-2 Horner runs on the conjugate, so
 // no negation is issued per ray.
-template <int MODE, int R, int Q, int K2, int BIN>
+template <int MODE, int R, int Q, int K2, int BIN, int NPR>
 __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpRayArgs& a, int64_t rc,
                                         int64_t want_i, int64_t want_j, int64_t work) {
   static_assert(R % 2 == 0, "rows go in pairs");
+  static_assert(NPR >= 0 && NPR <= R / 2, "paired row pairs");
   using L = IpSmem<Q, K2>;
   extern __shared__ __align__(16) unsigned char ip_smem[];
   float4* nxy_s = reinterpret_cast<float4*>(ip_smem + L::near_xy);
@@ -648,7 +653,13 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
       for (int i = 0; i < R / 2; ++i) {
         const float2 DY = __fadd2_rn(TY[i], NLY);
         const float2 R2 = __ffma2_rn(DY, DY, DX2);
-        const float2 W = __fmul2_rn(NM, make_float2(rcp_approx(R2.x), rcp_approx(R2.y)));
+        float2 W;
+        if (i < NPR) {  // -m/r_a^2 = -m r_b^2 / (r_a^2 r_b^2), and the same for b
+          const float mi = NM.x * rcp_approx(R2.x * R2.y);
+          W = __fmul2_rn(make_float2(R2.y, R2.x), make_float2(mi, mi));
+        } else {
+          W = __fmul2_rn(NM, make_float2(rcp_approx(R2.x), rcp_approx(R2.y)));
+        }
         NAX[i] = __ffma2_rn(W, DX, NAX[i]);
         NAY[i] = __ffma2_rn(W, DY, NAY[i]);
       }
@@ -781,11 +792,11 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
 }
 
 // One map: persistent grid over its ray cells (MAP) or requested rays (DUMP).
-template <int MODE, int R, int Q, int K2, int MINB, int BIN>
+template <int MODE, int R, int Q, int K2, int MINB, int BIN, int NPR>
 __global__ void __launch_bounds__(IP_THREADS, MINB) k_ip_ray(Geo g, IpGeo ig, IpRayArgs a) {
   for (int64_t work = blockIdx.x; work < a.nwork; work += gridDim.x) {
     if (MODE == IP_MAP) {
-      ip_cell<IP_MAP, R, Q, K2, BIN>(g, ig, a, a.rc_base + work, -1, -1, work);
+      ip_cell<IP_MAP, R, Q, K2, BIN, NPR>(g, ig, a, a.rc_base + work, -1, -1, work);
     } else {
       const int64_t f = a.idx[work];
       if (f < 0 || f >= g.nrx * g.nry) {  // not a lattice ray: report it, touch nothing else
@@ -796,7 +807,7 @@ __global__ void __launch_bounds__(IP_THREADS, MINB) k_ip_ray(Geo g, IpGeo ig, Ip
         continue;
       }
       const int64_t wi = f % g.nrx, wj = f / g.nrx;
-      ip_cell<IP_DUMP, R, Q, K2, BIN>(g, ig, a, (wj / ig.k) * ig.nrcx + wi / ig.k, wi, wj, work);
+      ip_cell<IP_DUMP, R, Q, K2, BIN, NPR>(g, ig, a, (wj / ig.k) * ig.nrcx + wi / ig.k, wi, wj, work);
     }
   }
 }
@@ -810,7 +821,7 @@ struct MapDesc {
   int64_t item0;  // index of the map's first item in the concatenated list
 };
 
-template <int R, int Q, int K2, int MINB, int BIN>
+template <int R, int Q, int K2, int MINB, int BIN, int NPR>
 __global__ void __launch_bounds__(IP_THREADS, MINB)
 k_ip_ray_batch(const MapDesc* __restrict__ maps, int nmaps, int64_t nitems,
                unsigned long long* __restrict__ queue) {
@@ -838,22 +849,22 @@ k_ip_ray_batch(const MapDesc* __restrict__ maps, int nmaps, int64_t nitems,
     __syncthreads();
     const long long it = item_s;
     if (it >= nitems) break;
-    ip_cell<IP_MAP, R, Q, K2, BIN>(md.g, md.ig, md.a, md.a.rc_base + (it - md.item0), -1, -1, it);
+    ip_cell<IP_MAP, R, Q, K2, BIN, NPR>(md.g, md.ig, md.a, md.a.rc_base + (it - md.item0), -1, -1, it);
   }
 }
 
 // Dynamic shared memory above the 48 KB default: set once per instantiation,
 // before any launch or graph capture that uses it.
-#define IP_DECL_ATTR(V, R, Q, K2, MINB, BIN)                                                           \
+#define IP_DECL_ATTR(V, R, Q, K2, MINB, BIN, NPR)                                                           \
   case V: {                                                                                            \
     const int b = (int)IpSmem<Q, K2>::bytes;                                                          \
-    e = cudaFuncSetAttribute(k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN>,                                   \
+    e = cudaFuncSetAttribute(k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR>,                                   \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, b);                         \
     if (e == cudaSuccess)                                                                              \
-      e = cudaFuncSetAttribute(k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN>,                                \
+      e = cudaFuncSetAttribute(k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN, NPR>,                                \
                                cudaFuncAttributeMaxDynamicSharedMemorySize, b);                       \
     if (e == cudaSuccess)                                                                              \
-      e = cudaFuncSetAttribute(k_ip_ray_batch<R, Q, K2, MINB, BIN>,                                   \
+      e = cudaFuncSetAttribute(k_ip_ray_batch<R, Q, K2, MINB, BIN, NPR>,                                   \
                                cudaFuncAttributeMaxDynamicSharedMemorySize, b);                       \
     break;                                                                                             \
   }
@@ -863,9 +874,9 @@ cudaError_t ip_ray_attributes(int variant) {
   return e;
 }
 
-#define IP_DECL_OCC(V, R, Q, K2, MINB, BIN)                                                       \
+#define IP_DECL_OCC(V, R, Q, K2, MINB, BIN, NPR)                                                       \
   case V:                                                                                         \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN>, \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR>, \
                                                   IP_THREADS, IpSmem<Q, K2>::bytes);              \
     break;
 int ip_ray_occupancy(int variant) {
@@ -874,13 +885,13 @@ int ip_ray_occupancy(int variant) {
   return per_sm > 0 ? per_sm : 1;
 }
 
-#define IP_DECL_LAUNCH(V, R, Q, K2, MINB, BIN)                                                           \
+#define IP_DECL_LAUNCH(V, R, Q, K2, MINB, BIN, NPR)                                                           \
   case V:                                                                                                \
     if (mode == IP_MAP)                                                                                  \
-      k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(g, ig, \
+      k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(g, ig, \
                                                                                                    a);   \
     else                                                                                                 \
-      k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(g,    \
+      k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(g,    \
                                                                                                  ig, a); \
     break;
 cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, const Geo& g,
@@ -889,9 +900,9 @@ cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, c
   return cudaGetLastError();
 }
 
-#define IP_DECL_BATCH(V, R, Q, K2, MINB, BIN)                                                       \
+#define IP_DECL_BATCH(V, R, Q, K2, MINB, BIN, NPR)                                                       \
   case V:                                                                                           \
-    k_ip_ray_batch<R, Q, K2, MINB, BIN><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(   \
+    k_ip_ray_batch<R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(   \
         maps, nmaps, nitems, queue);                                                                \
     break;
 cudaError_t launch_ip_ray_batch(int variant, int64_t grid, cudaStream_t s, const MapDesc* maps,
