@@ -471,6 +471,286 @@ def cpu_baseline(xy, m, w, target_s=15.0):
                       f"FP64 brute force) in {dt:.1f} s"}
 
 
+# ------------------------------------------------------------------ studies
+# Measurements the paper reports beside its speed figures, replayed on
+# synthetic lens fields: the accuracy-vs-rays slope (Sec. 3.3, fig. Accuracy),
+# the rectangular vs the circular lens plane (Sec. 2.2) and the deflection
+# perturbation behind the protective border (Sec. 2.3, fig. Proscale).
+
+def log_binned_rms(n, err, nbins=300, n_max=None, min_count=30):
+    """RMS of `err` in logarithmic bins of the per-pixel ray count `n` (n >= 1).
+    Returns (bin centres, rms, pixels per bin) for bins with >= min_count pixels."""
+    n = np.asarray(n, dtype=np.float64)
+    err = np.asarray(err, dtype=np.float64)
+    keep = n >= 1
+    n, err = n[keep], err[keep]
+    top = float(n_max if n_max else n.max())
+    edges = np.logspace(0.0, np.log10(top) + 1e-9, nbins + 1)
+    idx = np.clip(np.searchsorted(edges, n, side="right") - 1, 0, nbins - 1)
+    cnt = np.bincount(idx, minlength=nbins)
+    sq = np.bincount(idx, weights=err * err, minlength=nbins)
+    sn = np.bincount(idx, weights=n, minlength=nbins)
+    ok = cnt >= min_count
+    return sn[ok] / cnt[ok], np.sqrt(sq[ok] / cnt[ok]), cnt[ok]
+
+
+def loglog_slope(x, y, w=None):
+    """Least-squares slope of log10 y against log10 x (weights w)."""
+    lx, ly = np.log10(np.asarray(x, float)), np.log10(np.asarray(y, float))
+    w = np.ones_like(lx) if w is None else np.asarray(w, float)
+    mx, my = np.average(lx, weights=w), np.average(ly, weights=w)
+    return float(np.sum(w * (lx - mx) * (ly - my)) / np.sum(w * (lx - mx) ** 2))
+
+
+def katz_density(u, n_lens, c=1.454, npts=20001):
+    """Density per unit area of the deflection perturbation in units of
+    phi_0 = sqrt(kappa_*): Katz et al.'s Eq. 13 with numerator c (3.05 in
+    Katz; 1.454 in the paper's modified form, Sec. 2.3):
+        rho(u) = (1/2pi) int_0^x* x J0(x u) exp[-(x^2/2) ln(c sqrt(N)/x)] dx.
+    The form is asymptotic: the exponent is most negative at
+    x* = c sqrt(N) e^-1/2 (where it equals -x*^2/4) and rises beyond, so the
+    integral stops there, or earlier where the integrand is below e^-60."""
+    from scipy.special import j0
+    xs = c * np.sqrt(n_lens) * np.exp(-0.5)
+    # end where the integrand is below e^-60, if that comes before x*
+    xg = np.linspace(1e-6, xs, 100001)
+    past = np.nonzero(0.5 * xg * xg * np.log(c * np.sqrt(n_lens) / xg) > 60.0)[0]
+    x = np.linspace(0.0, xg[past[0]] if past.size else xs, npts)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ex = np.where(x > 0, -0.5 * x * x * np.log(c * np.sqrt(n_lens) / np.maximum(x, 1e-300)), 0.0)
+    g = x * np.exp(ex)
+    u = np.atleast_1d(np.asarray(u, float))
+    vals = np.trapezoid(g[None, :] * j0(np.outer(u, x)), x, axis=1)
+    return vals / (2.0 * np.pi)
+
+
+def _study_env():
+    import torch
+    from paper_2204_10871_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2204_10871_gb300 import irs, lensgen
+    torch.cuda.set_device(0)
+    return torch, irs, lensgen
+
+
+def _interp_map(irs, torch, params, dxy, dm, rows=None):
+    shape = (params.npix_y, params.npix_x)
+    counts = torch.zeros(shape, dtype=torch.uint32, device=dxy.device)
+    with irs.Plan(params) as plan:
+        irs.irs_plan_set_timing(plan.handle, True)
+        if rows is None:
+            irs.irs_make_map(plan.handle, dxy, dm, counts)
+        else:
+            irs.irs_make_map_rows(plan.handle, dxy, dm, rows[0], rows[1], counts)
+        t = irs.irs_plan_timings(plan.handle)
+        plan.sync()
+        info = plan.info
+    return counts.cpu().numpy().astype(np.float64), t, info
+
+
+def study_accuracy(args):
+    """Sec. 3.3: kappa = kappa_* = 0.652, gamma = 0, 50 theta_E at 1024^2, 1e5
+    uniform-mass lenses; maps of (10240 k)^2 rays, k = 1..7, against a map of
+    ~4e10 rays; RMS relative magnification error in 300 log bins of the
+    per-pixel ray count, and its log-log slope (paper: about -2/3)."""
+    torch, irs, lensgen = _study_env()
+    ks, S, npix = 0.652, 50.0, 1024
+    src = (-S / 2, S / 2, -S / 2, S / 2)
+    n_star = 100000
+    base = irs.make_params(ks, 0.0, 0.0, src, npix, 1.0, n_star=n_star, method=irs.IRS_INTERP)
+    with irs.Plan(base) as pr:
+        inf = pr.info
+    box = (inf.lens_x0, inf.lens_x1, inf.lens_y0, inf.lens_y1)
+    area = (box[1] - box[0]) * (box[3] - box[2])
+    xy, m = lensgen.lens_field(n_star, box, shape="uniform", seed=7, total_mass=ks * area / np.pi)
+    dxy, dm = torch.from_numpy(xy).cuda(), torch.from_numpy(m).cuda()
+    s2 = (S / npix) ** 2
+
+    def params(n_rays, method=irs.IRS_INTERP):
+        return irs.make_params(ks, 0.0, 0.0, src, npix, n_rays * s2 / area, n_star=n_star, method=method,
+                               kernel_variant=7 if method == irs.IRS_INTERP else 0)
+
+    ref_rays = args.ref_rays
+    ref, tref, iref = _interp_map(irs, torch, params(ref_rays), dxy, dm)
+    nav_ref = ref_rays * s2 / area
+    # the reference's own method error: the brute force on a band of its rays
+    r0 = iref.n_rays_y // 2
+    band = (r0, r0 + 64)
+    pb = params(ref_rays, irs.IRS_BRUTE)
+    bb, _, _ = _interp_map(irs, torch, pb, dxy, dm, rows=band)
+    bi, _, _ = _interp_map(irs, torch, params(ref_rays), dxy, dm, rows=band)
+    sel = bb >= 100
+    band_rms = float(np.sqrt(np.mean(((bi[sel] - bb[sel]) / bb[sel]) ** 2))) if sel.any() else None
+    maps, allx, ally, allw = [], [], [], []
+    for k in range(1, 8):
+        n_rays = (10240 * k) ** 2
+        c, t, info = _interp_map(irs, torch, params(n_rays), dxy, dm)
+        nav = n_rays * s2 / area
+        ok = ref > 0
+        err = (c[ok] / nav) / (ref[ok] / nav_ref) - 1.0
+        x, y, w = log_binned_rms(c[ok], err, nbins=300, n_max=None, min_count=30)
+        fit = x >= 10
+        maps.append({"n_rays_target": n_rays, "n_rays": int(info.n_rays), "rays_per_unlensed_pixel": nav,
+                     "mean_rays_per_pixel": float(c.mean()), "ms_map": t.ms_total,
+                     "rel_rms_all_pixels": float(np.sqrt(np.mean(err[c[ok] > 0] ** 2))),
+                     "slope": loglog_slope(x[fit], y[fit], w[fit]) if fit.sum() > 2 else None,
+                     "bins": int(len(x))})
+        allx.append(x[fit]); ally.append(y[fit]); allw.append(w[fit])
+    X, Y, Wt = np.concatenate(allx), np.concatenate(ally), np.concatenate(allw)
+    out = {"study": "accuracy", "config": {"kappa": ks, "kappa_star": ks, "gamma": 0.0, "S": S, "npix": npix,
+                                           "n_star": n_star, "masses": "uniform 0.1-1 rescaled to kappa_*",
+                                           "method": "interp variant 7", "bins": 300, "min_pixels_per_bin": 30,
+                                           "fit": "bins with >= 10 rays per pixel"},
+           "reference": {"n_rays": int(iref.n_rays), "rays_per_unlensed_pixel": nav_ref, "ms_map": tref.ms_total,
+                         "interp_vs_brute_band_rel_rms": band_rms, "band_rows": list(band),
+                         "band_pixels_ge_100_rays": int(sel.sum())},
+           "maps": maps, "slope_all_maps": loglog_slope(X, Y, Wt), "paper_slope": -2.0 / 3.0}
+    print(json.dumps(out))
+
+
+def study_planes(args):
+    """Sec. 2.2: the rectangular lens plane against the circumscribed circle
+    at the paper-mid workload (kappa_* = gamma = 0.45): lenses needed at the
+    same density, and the time of a full map (interpolated) and of the brute
+    force (per ray, on a band)."""
+    torch, irs, lensgen = _study_env()
+    w = WORKLOAD
+    res = {}
+    for name, plane in (("rect", irs.IRS_PLANE_RECT), ("circle", irs.IRS_PLANE_CIRCLE)):
+        S = w["S"]
+        src = (-S / 2, S / 2, -S / 2, S / 2)
+        p = irs.make_params(w["kappa_star"], w["kappa_s"], w["gamma"], src, w["npix"], w["nav"],
+                            n_star=w["n_star"], plane=plane, method=irs.IRS_INTERP, kernel_variant=7)
+        with irs.Plan(p) as pr:
+            inf = pr.info
+        rect_area = (inf.lens_x1 - inf.lens_x0) * (inf.lens_y1 - inf.lens_y0)
+        if plane == irs.IRS_PLANE_CIRCLE:
+            area = np.pi * inf.circle_r ** 2
+            n = int(round(w["n_star"] * area / res["rect"]["lens_area"]))
+            xy, m = lensgen.lens_field(n, None, shape=w["shape"], seed=w["seed"],
+                                       total_mass=w["kappa_star"] * area / np.pi,
+                                       disc=(inf.center_x, inf.center_y, inf.circle_r))
+        else:
+            area = rect_area
+            n = w["n_star"]
+            xy, m = lensgen.lens_field(n, (inf.lens_x0, inf.lens_x1, inf.lens_y0, inf.lens_y1), shape=w["shape"],
+                                       seed=w["seed"], total_mass=w["kappa_star"] * area / np.pi)
+        p.n_star = n
+        dxy, dm = torch.from_numpy(xy).cuda(), torch.from_numpy(m).cuda()
+        ms = []
+        for it in range(3):
+            _, t, info = _interp_map(irs, torch, p, dxy, dm)
+            if it:
+                ms.append((t.ms_total, t.ms_raypass, t.ms_farfield))
+        pb = irs.make_params(w["kappa_star"], w["kappa_s"], w["gamma"], src, w["npix"], w["nav"],
+                             n_star=n, plane=plane, method=irs.IRS_BRUTE)
+        r0 = info.n_rays_y // 2
+        band = (r0 - r0 % 64, r0 - r0 % 64 + 64)
+        bt = []
+        for it in range(2):
+            _, t, _ = _interp_map(irs, torch, pb, dxy, dm, rows=band)
+            bt.append(t.ms_raypass)
+        rays_band = (band[1] - band[0]) * info.n_rays_x
+        res[name] = {"lenses": n, "lens_area": area, "image_rect_area": rect_area,
+                     "cells": int(info.ncell_x) * int(info.ncell_y), "n_rays": int(info.n_rays),
+                     "interp_ms_map": float(np.mean([a for a, _, _ in ms])),
+                     "interp_ms_raypass": float(np.mean([b for _, b, _ in ms])),
+                     "interp_ms_far_field": float(np.mean([c for _, _, c in ms])),
+                     "brute_rays_per_s": rays_band / (bt[-1] * 1e-3),
+                     "brute_ms_map_extrapolated": info.n_rays / (rays_band / bt[-1])}
+    out = {"study": "planes", "workload": w["name"], "rect": res["rect"], "circle": res["circle"],
+           "lens_ratio": res["circle"]["lenses"] / res["rect"]["lenses"],
+           "interp_time_ratio": res["circle"]["interp_ms_map"] / res["rect"]["interp_ms_map"],
+           "brute_time_ratio": res["circle"]["brute_ms_map_extrapolated"] / res["rect"]["brute_ms_map_extrapolated"]}
+    print(json.dumps(out))
+
+
+def study_border(args):
+    """Sec. 2.3: (1) the distribution of the deflection perturbation (lens sum
+    plus negative sheet, Eq. alpha1) in the central quarter of the plane for
+    N = 1e2 ... 1e6 unit-mass lenses, kappa_* = 0.4, gamma = 0, pooled over
+    several lens fields, against Katz's Eq. 13 with the numerator 3.05 and the
+    paper's 1.454, and the fraction beyond the 10 phi_0 border; (2) the
+    fraction of the needed rays that the bordered plane delivers (map mean
+    over <mu>) at the paper-mid workload, over 8 fields."""
+    torch, irs, lensgen = _study_env()
+    kst = 0.4
+    phi0 = np.sqrt(kst)
+    pdf = []
+    edges = np.linspace(0.0, 12.0, 49)
+    uc = 0.5 * (edges[1:] + edges[:-1])
+    ring = np.pi * (edges[1:] ** 2 - edges[:-1] ** 2)
+    for n, fields in ((100, 16), (1000, 16), (10000, 8), (1000000, 2)):
+        P = 10.0 * phi0
+        S = float(np.sqrt(np.pi * n / kst) * (1.0 - kst) - 2.0 * P)
+        src = (-S / 2, S / 2, -S / 2, S / 2)
+        p = irs.make_params(kst, 0.0, 0.0, src, 64, 64.0, n_star=n, method=irs.IRS_BRUTE)
+        k = 400000 // fields  # rays per field
+        us = []
+        with irs.Plan(p) as plan:
+            inf = plan.info
+            box = (inf.lens_x0, inf.lens_x1, inf.lens_y0, inf.lens_y1)
+            nx, ny = inf.n_rays_x, inf.n_rays_y
+            for f in range(fields):
+                xy, m = lensgen.lens_field(n, box, shape="equal", seed=11 + 1000 * f)
+                dxy, dm = torch.from_numpy(xy).cuda(), torch.from_numpy(m).cuda()
+                # rays in the central quarter of the plane (deep inside the field)
+                rng = np.random.Generator(np.random.PCG64(5 + f))
+                i = rng.integers(nx // 4, 3 * nx // 4, k)
+                j = rng.integers(ny // 4, 3 * ny // 4, k)
+                idx = torch.from_numpy(j * nx + i).cuda()
+                beta = torch.empty((k, 2), dtype=torch.float64, device="cuda")
+                irs.irs_shoot_rays(plan.handle, dxy, dm, idx, beta)
+                plan.sync()
+                b = beta.cpu().numpy()
+                th = np.stack([inf.lens_x0 + (i + 0.5) * inf.dx_ray, inf.lens_y0 + (j + 0.5) * inf.dx_ray], 1)
+                kap = np.pi * m.sum() / ((box[1] - box[0]) * (box[3] - box[2]))  # actual kappa_* (R2)
+                ap = th * (1.0 - kap) - b  # alpha - kappa theta: lens sum + negative sheet
+                us.append(np.hypot(ap[:, 0], ap[:, 1]) / phi0)
+        u = np.concatenate(us)
+        h, _ = np.histogram(u, bins=edges)
+        dens = h / (u.size * ring)
+        dmod = katz_density(uc, n, 1.454)
+        dkat = katz_density(uc, n, 3.05)
+        cdf_e = np.cumsum(h) / u.size
+        pdf.append({"n_lens": n, "S": S, "fields": fields, "rays": int(u.size),
+                    "frac_beyond_4phi0": float(np.mean(u > 4)), "frac_beyond_10phi0": float(np.mean(u > 10)),
+                    "density_near_10phi0": float(dens[np.searchsorted(uc, 10.0)]),
+                    "median_u": float(np.median(u)),
+                    "cdf_max_dev_modified_katz": float(np.max(np.abs(cdf_e - np.cumsum(dmod * ring)))),
+                    "cdf_max_dev_katz": float(np.max(np.abs(cdf_e - np.cumsum(dkat * ring)))),
+                    "u": [round(float(x), 3) for x in uc[::4]],
+                    "density": [float(x) for x in dens[::4]],
+                    "modified_katz": [float(x) for x in dmod[::4]], "katz": [float(x) for x in dkat[::4]]})
+    # ray capture at the paper-mid workload
+    w = WORKLOAD
+    S = w["S"]
+    src = (-S / 2, S / 2, -S / 2, S / 2)
+    p = irs.make_params(w["kappa_star"], w["kappa_s"], w["gamma"], src, w["npix"], w["nav"],
+                        n_star=w["n_star"], method=irs.IRS_INTERP, kernel_variant=7)
+    cap = []
+    with irs.Plan(p) as plan:
+        inf = plan.info
+        box = (inf.lens_x0, inf.lens_x1, inf.lens_y0, inf.lens_y1)
+        area = (box[1] - box[0]) * (box[3] - box[2])
+        counts = torch.zeros((w["npix"], w["npix"]), dtype=torch.uint32, device="cuda")
+        for seed in range(8):
+            xy, m = lensgen.lens_field(w["n_star"], box, shape=w["shape"], seed=100 + seed,
+                                       total_mass=w["kappa_star"] * area / np.pi)
+            dxy, dm = torch.from_numpy(xy).cuda(), torch.from_numpy(m).cuda()
+            irs.irs_make_map(plan.handle, dxy, dm, counts)
+            plan.sync()
+            landed = float(counts.sum(dtype=torch.float64).item())
+            kap = w["kappa_s"] + np.pi * m.sum() / area
+            mu0 = 1.0 / abs((1.0 - kap) ** 2 - w["gamma"] ** 2)
+            cap.append(landed / (w["npix"] ** 2 * w["nav"] * mu0))
+    out = {"study": "border", "kappa_star": kst, "gamma": 0.0, "phi0": phi0, "pdf": pdf,
+           "capture": {"workload": w["name"], "fields": len(cap), "fraction_mean": float(np.mean(cap)),
+                       "fraction_sem": float(np.std(cap, ddof=1) / np.sqrt(len(cap))),
+                       "fractions": cap, "paper_claim": "> 0.98"}}
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     world, rank, local = dist_init()
@@ -530,10 +810,15 @@ def main():
     ap.add_argument("--n-star", type=int, default=0, help="override the lens count (profiling)")
     ap.add_argument("--npix", type=int, default=0, help="override the map side (profiling)")
     ap.add_argument("--nav", type=float, default=0.0, help="override rays per pixel (profiling)")
+    ap.add_argument("--study", default="", choices=["", "accuracy", "planes", "border"],
+                    help="one of the paper's side measurements instead of the benchmark (one GPU)")
+    ap.add_argument("--ref-rays", type=float, default=4.0e10, help="rays of the accuracy study's reference map")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.study:
+        {"accuracy": study_accuracy, "planes": study_planes, "border": study_border}[args.study](args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
