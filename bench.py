@@ -13,9 +13,15 @@ lattice rows through irs_make_map_rows and reported per ray, with the same
 band made by the interpolated method as the accuracy check (per-pixel
 magnification relative RMS over pixels with >= 100 rays).
 
-Multi-GPU: maps are independent problems, so each rank makes its own map
-(weak scaling, no collective on the data path); value = all ranks' rays / the
-slowest rank's time.
+Multi-GPU: maps are independent problems, so by default each rank makes its
+own map (weak scaling, no collective on the data path); value = all ranks'
+rays / the slowest rank's time.  --shard strips makes ONE map over all ranks
+(strong scaling): each rank shoots a strip of whole cell rows and the count
+maps are summed (one all-reduce per map, inside the timed step).
+
+--study accuracy | planes | border replays the paper's accuracy-vs-rays slope,
+its rectangular vs circular lens plane comparison and its protective-border
+deflection distribution (one GPU; one JSON line each).
 
 --impl reference times the FP64 CPU oracle (the plain definition the GPU path
 is checked against) on a bounded sample of the same workload on the host
@@ -219,7 +225,9 @@ def run_ours(args):
     probe = irs.Plan(params)  # the lens plane does not depend on the tuning
     box = (probe.info.lens_x0, probe.info.lens_x1, probe.info.lens_y0, probe.info.lens_y1)
     probe.close()
-    xy, m = lens_field(lensgen, box, w["seed"] + 1000 * rank, w)
+    sharded = args.shard == "strips" and full
+    # replicas: a map per rank (own lens field); strips: one map over all ranks
+    xy, m = lens_field(lensgen, box, w["seed"] + (0 if sharded else 1000 * rank), w)
     dxy = torch.from_numpy(xy).to(dev)
     dm = torch.from_numpy(m).to(dev)
     tune = None
@@ -250,14 +258,22 @@ def run_ours(args):
     r0 = (info.n_rays_y // 2 // 64) * 64  # whole brute tiles (64 rows)
     band = (r0, min(info.n_rays_y, r0 + band_rows))
 
+    from paper_2204_10871_gb300 import shard
+
     def step():
-        if full:
+        if sharded:  # this rank's strip of rows, then the sum of the count maps
+            shard.make_map_sharded(plan, dxy, dm, counts, world, rank, mag=mag)
+        elif full:
             irs.irs_make_map(plan.handle, dxy, dm, counts, mag)
         else:
             counts.zero_()
             irs.irs_make_map_rows(plan.handle, dxy, dm, band[0], band[1], counts)
 
     rays_per_step = info.n_rays if full else (band[1] - band[0]) * info.n_rays_x
+    my_rays = rays_per_step  # rays this rank shoots per step
+    if sharded:
+        s0, s1 = shard.strip_rows(int(info.n_rays_y), world, rank, shard.row_align(plan))
+        my_rays = (s1 - s0) * info.n_rays_x
     for _ in range(args.warmup):
         step()
     plan.sync()
@@ -288,7 +304,8 @@ def run_ours(args):
         my_ms = slowest_rank_ms(my_ms, dist, dev)
         dist.barrier()
     ms_per_step = my_ms / args.steps
-    value = whole_job_rays_per_s(rays_per_step, world, ms_per_step)
+    value = (rays_per_step / (ms_per_step * 1e-3) if sharded
+             else whole_job_rays_per_s(rays_per_step, world, ms_per_step))
 
     # ---- end to end through the public API with host buffers
     h_xy = torch.from_numpy(xy).pin_memory()
@@ -306,6 +323,10 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        e2e_ms = slowest_rank_ms(e2e_ms, dist, dev)
+    e2e_value = (rays_per_step / (e2e_ms * 1e-3) if sharded
+                 else whole_job_rays_per_s(rays_per_step, world, e2e_ms))
     h2d = xy.nbytes + m.nbytes
     d2h = h_counts.numel() * 4
     clocks = clk.summary()
@@ -328,7 +349,7 @@ def run_ours(args):
         n_near = None
         flops_per_ray = 10.0 * w["n_star"]
         kname = "k_brute (pair sum, FP32 pipe + MUFU)"
-    achieved = flops_per_ray * rays_per_step / (ray_ms_mean * 1e-3) / 1e12
+    achieved = flops_per_ray * my_rays / (ray_ms_mean * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                 "peak_basis": f"{n_sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
@@ -364,7 +385,8 @@ def run_ours(args):
             "metric": "rays/s per GB300 (" + args.method + ")",
             "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (pairs), f64 (far field, setup)",
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+            "dtype": "f32 (pairs), f64 (far field, setup)",
             "data": "synthetic (seeded lens fields; the paper's lens catalogues are not public)",
             "config": {"workload": w["name"] if not (args.n_star or args.npix or args.nav)
                        else "reduced case for profiling", "method": args.method,
@@ -372,8 +394,8 @@ def run_ours(args):
                        "rays_per_pixel": w["nav"],
                        "band_rows": None if full else [int(band[0]), int(band[1])],
                        "l2": "flushed between steps (512 MB write)",
-                       "parallelism": f"replicas x{world}"},
-            "e2e": {"value": rays_per_step / (e2e_ms * 1e-3), "unit": "rays/s",
+                       "parallelism": f"{'strips' if sharded else 'replicas'} x{world}"},
+            "e2e": {"value": e2e_value, "unit": "rays/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "autotune": tune,
@@ -704,7 +726,7 @@ def study_border(args):
                 plan.sync()
                 b = beta.cpu().numpy()
                 th = np.stack([inf.lens_x0 + (i + 0.5) * inf.dx_ray, inf.lens_y0 + (j + 0.5) * inf.dx_ray], 1)
-                kap = np.pi * m.sum() / ((box[1] - box[0]) * (box[3] - box[2]))  # actual kappa_* (R2)
+                kap = np.pi * m.sum() / ((box[1] - box[0]) * (box[3] - box[2]))  # kappa_* of the lenses passed in, pi sum(m) / A
                 ap = th * (1.0 - kap) - b  # alpha - kappa theta: lens sum + negative sheet
                 us.append(np.hypot(ap[:, 0], ap[:, 1]) / phi0)
         u = np.concatenate(us)
@@ -813,6 +835,8 @@ def main():
     ap.add_argument("--study", default="", choices=["", "accuracy", "planes", "border"],
                     help="one of the paper's side measurements instead of the benchmark (one GPU)")
     ap.add_argument("--ref-rays", type=float, default=4.0e10, help="rays of the accuracy study's reference map")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "strips"],
+                    help="N > 1: a map per rank (weak scaling) or one map in row strips (strong)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

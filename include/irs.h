@@ -142,9 +142,12 @@ irs_status irs_make_maps_batched(irs_plan_t* const* plans, int32_t nmaps,
 
 /* Chunked sweep (the count map is additive over disjoint sets of rays): add
  * into `counts` (device, NOT cleared) the rays of lattice rows
- * [row0, row1) only.  Used to sweep very large lattices in pieces and to
- * resume a sweep from a saved map plus the next row.  The sheet density and
- * all per-map constants are recomputed from the lenses on every call.
+ * [row0, row1) only.  Used to sweep very large lattices in pieces, to resume
+ * a sweep from a saved map plus the next row, and to split one map over
+ * several GPUs (each shoots a strip of rows; the count maps are summed).  The
+ * sheet density and all per-map constants are recomputed from the lenses on
+ * every call; INTERP computes the per-cell series only for the level-1 cell
+ * rows the band touches (the global far-field convolution is always whole).
  * Errors: IRS_ERR_ARG (row range outside [0, n_rays_y]), as irs_make_map. */
 irs_status irs_make_map_rows(irs_plan_t* plan, const double* lens_xy, const double* mass,
                              int64_t n, int64_t row0, int64_t row1, uint32_t* counts,
@@ -167,6 +170,7 @@ typedef struct irs_timings {
   int64_t rays;       /* rays shot by the timed map */
   int32_t valid;      /* 1 when the fields hold a measurement */
   int32_t launches;   /* kernel launches of the map */
+  float ms_finalize;  /* INTERP: the per-cell part of ms_farfield (window, sheet series) */
 } irs_timings;
 
 irs_status irs_plan_set_timing(irs_plan_t* plan, int32_t enable);

@@ -92,7 +92,7 @@ def make_params(kappa_star, kappa_s, gamma, src, npix, rays_per_pixel, border=-1
 
 
 def size(params: OracleParams) -> OraclePlan:
-    """Sizing of the image/lens plane and the ray lattice (flow chart, reading R3)."""
+    """Sizing of the image/lens plane and the ray lattice (flow chart; N_av counts rays per unlensed source pixel)."""
     plan = OraclePlan()
     rc = _L().or_size(C.byref(params), C.byref(plan))
     if rc == 1:

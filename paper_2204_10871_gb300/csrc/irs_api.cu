@@ -149,6 +149,7 @@ irs_status run_map(irs_plan_t* P, const double* xy, const double* mass, int64_t 
     IRS_TRY(irs::launch_brute_setup(P, s));
     mark(P, irs::EV_PREP, s);
     mark(P, irs::EV_CELLS, s);
+    mark(P, irs::EV_FIN, s);
     mark(P, irs::EV_FAR, s);
     mark(P, irs::EV_RAY0, s);
     IRS_TRY(irs::launch_brute_map(P, xy, mass, n, row0, row1, counts, s));
@@ -293,6 +294,7 @@ irs_status irs_plan_timings(irs_plan_t* P, irs_timings* out) {
   out->ms_farfield = ms(irs::EV_CELLS, irs::EV_FAR);
   out->ms_raypass = ms(irs::EV_RAY0, irs::EV_RAY1);
   out->ms_magnify = P->has_mag ? ms(irs::EV_MAG, irs::EV_END) : 0.f;
+  out->ms_finalize = ms(irs::EV_FIN, irs::EV_FAR);
   out->rays = P->timed_rays;
   out->launches = P->launches;
   out->valid = 1;

@@ -107,9 +107,12 @@ double measure(const irs_params& base, double mult, int variant, const double* x
     if (irs_make_map_rows(P, xy, mass, n, r0, r1, counts, s) != IRS_OK) break;
     irs_timings t;
     if (irs_plan_timings(P, &t) != IRS_OK || !t.valid) break;
-    if (rep == 1) {
+    if (rep == 1) {  // the band's ray pass and per-cell series scaled to the whole lattice
       const double scale = (double)info.n_rays_y / (double)(r1 - r0);
-      est = (double)(t.ms_total - t.ms_raypass) + (double)t.ms_raypass * scale;
+      const int64_t k = info.rays_per_cell_y;
+      const double cell_scale = (double)((info.n_rays_y + k - 1) / k) / (double)((r1 + k - 1) / k - r0 / k);
+      est = (double)(t.ms_total - t.ms_raypass - t.ms_finalize) + (double)t.ms_finalize * cell_scale +
+            (double)t.ms_raypass * scale;
     }
   }
   if (irs_plan_sync(P, s) != IRS_OK) est = -1.0;

@@ -84,7 +84,7 @@ __global__ void k_brute_setup(Geo g, const double* __restrict__ msum, int64_t nt
   const int64_t tile = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tile >= ntiles) return;
   const TileGeo tg = tile_geo(g, tile, ntx);
-  const double ks = g.kstar_scale * msum[0];  // kappa_*^act (reading R2)
+  const double ks = g.kstar_scale * msum[0];  // kappa_*^act = pi sum(m) / A of the lenses passed in
   const double kap = g.kappa_s + ks;
   const double zx = g.a1 + tg.ci * g.dx3, zy = g.b1 + tg.cj * g.dx3;
 

@@ -150,6 +150,11 @@ __device__ __forceinline__ TileGeo tile_geo(const Geo& g, int64_t tile, int64_t 
 }  // namespace irs
 
 // ---------------------------------------------------------------- host side
+namespace irs {
+// timing event slots of irs_plan::ev
+enum { EV_START = 0, EV_PREP, EV_CELLS, EV_FIN, EV_FAR, EV_RAY0, EV_RAY1, EV_MAG, EV_END, EV_COUNT };
+}  // namespace irs
+
 struct irs_plan {
   irs_params p;
   irs::Geo g;
@@ -174,16 +179,11 @@ struct irs_plan {
   void* mlp;
   // stage timing (irs_plan_set_timing)
   int timing;
-  cudaEvent_t ev[8];
+  cudaEvent_t ev[irs::EV_COUNT];
   int64_t timed_rays;
   int has_mag;
   int launches;  // kernel launches of the last map
 };
-
-namespace irs {
-// timing event slots of irs_plan::ev
-enum { EV_START = 0, EV_PREP, EV_CELLS, EV_FAR, EV_RAY0, EV_RAY1, EV_MAG, EV_END, EV_COUNT };
-}  // namespace irs
 
 namespace irs {
 constexpr int MSUM_BLOCKS = 128;

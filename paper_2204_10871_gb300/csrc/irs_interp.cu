@@ -283,14 +283,14 @@ __global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, double2* __restr
   for (int k = 0; k < IP_P; ++k) spec[(int64_t)k * G + f] = make_double2(Cc[k].re, Cc[k].im);
 }
 
-// Per ray cell: window P2L, M2L result, sheet series, centre term, base pixel.
+// Per ray cell of [rc0, rc1): window P2L, M2L result, sheet series, centre
+// term, base pixel.
 __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
                               const int32_t* __restrict__ start, const double2* __restrict__ pos,
                               const double* __restrict__ m, const double2* __restrict__ conv, MlpFar far,
-                              CellRec* __restrict__ recs, float2* __restrict__ coef) {
-  const int64_t rc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nrc = (int64_t)ig.nrcx * ig.nrcy;
-  if (rc >= nrc) return;
+                              CellRec* __restrict__ recs, float2* __restrict__ coef, int64_t rc0, int64_t rc1) {
+  const int64_t rc = rc0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (rc >= rc1) return;
   const int cx = (int)(rc % ig.nrcx) + ig.ox, cy = (int)(rc / ig.nrcx) + ig.oy;
   const int64_t ncells = (int64_t)ig.ncx * ig.ncy;
   const int64_t c = (int64_t)cy * ig.ncx + cx;
@@ -961,8 +961,10 @@ void mark(irs_plan_t* P, int slot, cudaStream_t s) {
 // kernel launches of one map, reported through irs_plan_timings
 int far_launches(int64_t n) { return (n > 0 ? 4 : 0) + 3 + 1 + 2 + 1 + 2 + 1; }  // series mode
 
+// Cell lists and far field; the per-cell finalize covers ray cells
+// [rc0, rc1) only (rc1 < 0: all of them).
 irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* mass, int64_t n,
-                               cudaStream_t s) {
+                               cudaStream_t s, int64_t rc0 = 0, int64_t rc1 = -1) {
   InterpState* S = S_(P);
   const IpGeo& ig = S->ig;
   const int64_t ncells = (int64_t)ig.ncx * ig.ncy;
@@ -1004,8 +1006,12 @@ irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* ma
     IP_TRY(fft2d_inverse(S->spec, S->fft, ig.ncx, ig.ncy, S->conv, ncells, ig.P, s));
   }
   const int64_t nrc = (int64_t)ig.nrcx * ig.nrcy;
-  k_ip_finalize<<<(unsigned)((nrc + 63) / 64), 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start, S->lens_pos,
-                                                          S->lens_m, S->conv, far, S->recs, S->coef);
+  if (rc1 < 0 || rc1 > nrc) rc1 = nrc;
+  mark(P, EV_FIN, s);
+  if (rc1 > rc0)
+    k_ip_finalize<<<(unsigned)((rc1 - rc0 + 63) / 64), 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start,
+                                                                   S->lens_pos, S->lens_m, S->conv, far,
+                                                                   S->recs, S->coef, rc0, rc1);
   IP_TRY(cudaGetLastError());
   mark(P, EV_FAR, s);
   return IRS_OK;
@@ -1155,17 +1161,19 @@ irs_status interp_run(irs_plan_t* P, const double* xy, const double* mass, int64
                       int64_t row1, uint32_t* counts, cudaStream_t s) {
   InterpState* S = S_(P);
   mark(P, EV_PREP, s);
-  irs_status st = build_cells_and_far(P, xy, mass, n, s);
+  // only the cell rows the band touches need their series
+  const int64_t k = S->ig.k;
+  const int64_t rc0 = row1 > row0 ? (row0 / k) * S->ig.nrcx : 0;
+  const int64_t rc1 = row1 > row0 ? ((row1 + k - 1) / k) * S->ig.nrcx : 0;
+  irs_status st = build_cells_and_far(P, xy, mass, n, s, rc0, rc1);
   if (st != IRS_OK) return st;
   mark(P, EV_RAY0, s);
-  P->launches += far_launches(n) + (row1 > row0 ? 1 : 0);
+  P->launches += far_launches(n) - (rc1 > rc0 ? 0 : 1) + (row1 > row0 ? 1 : 0);
   if (row1 > row0) {
     IpRayArgs a = ray_args(P);
     a.counts = counts;
     a.row0 = row0;
     a.row1 = row1;
-    const int64_t k = S->ig.k;
-    const int64_t rc0 = (row0 / k) * S->ig.nrcx, rc1 = ((row1 + k - 1) / k) * S->ig.nrcx;
     a.rc_base = rc0;
     a.nwork = rc1 - rc0;
     const int64_t grid = (rc1 - rc0) < S->grid_ray ? (rc1 - rc0) : S->grid_ray;

@@ -50,7 +50,8 @@ class IrsPlanInfo(C.Structure):
 class IrsTimings(C.Structure):
     _fields_ = [("ms_total", C.c_float), ("ms_prep", C.c_float), ("ms_cells", C.c_float),
                 ("ms_farfield", C.c_float), ("ms_raypass", C.c_float), ("ms_magnify", C.c_float),
-                ("rays", C.c_int64), ("valid", C.c_int32), ("launches", C.c_int32)]
+                ("rays", C.c_int64), ("valid", C.c_int32), ("launches", C.c_int32),
+                ("ms_finalize", C.c_float)]
 
 
 class IrsTuneResult(C.Structure):

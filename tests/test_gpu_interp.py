@@ -135,8 +135,8 @@ def test_interp_edge_cases():
     plane (cell grid over the circle's bounding box); repeat determinism."""
     torch = require_gpu()
     # 16.3 rays per pixel: a lattice incommensurate with the pixels, so that no
-    # lens-free ray lands exactly on a pixel edge (reading R7 leaves those to
-    # rounding, FP64 in the oracle, FP32 here)
+    # lens-free ray lands exactly on a pixel edge (the floor binning leaves those
+    # to rounding, FP64 in the oracle, FP32 here)
     cfg = (0.3, 0.1, 0.2, (-1.0, 1.0, -1.0, 1.0), 40, 16.3)
     po, pl = params_pair(*cfg, method=irs.IRS_INTERP)
     qo = oracle.size(po)

@@ -91,7 +91,7 @@ def _field(params, plan, n, shape="equal", seed=1):
 def test_deflection_divergence_is_kappa_s():
     """Eq. (alpha1): away from lenses the lens sum is divergence free, the
     matrix term gives 2 kappa and the NEGATIVE sheet -2 kappa_*, so
-    div(alpha) = 2 kappa_s.  Catches a positive sheet (reading R1) or a matrix
+    div(alpha) = 2 kappa_s.  Catches a positive sheet (the appendix's sign taken as is) or a matrix
     that forgets kappa_*."""
     p = oracle.make_params(0.35, 0.15, 0.4, (-1.0, 1.0, -1.0, 1.0), 16, 4.0)
     q = oracle.size(p)
@@ -188,7 +188,7 @@ def test_point_lens_paczynski():
 def test_lens_free_sheet_counts(ks, kstar, g):
     """No lenses: the map is the linear smooth mapping diag(1-k-g, 1-k+g) of a
     regular lattice (Eq. lensequation with N_* = 0; declared kappa_* without
-    lenses adds nothing, reading R2).  Each pixel holds between
+    lenses adds nothing: the sheet uses the density of the lenses passed in).  Each pixel holds between
     floor(wx)floor(wy) and ceil(wx)ceil(wy) rays, w = s / (|lambda| dx3), and
     the mean magnification is 1/|(1-k)^2 - g^2|."""
     p = oracle.make_params(kstar, ks, g, (-1.0, 1.5, -1.2, 0.8), (24, 16), 37.0)
@@ -252,7 +252,7 @@ def test_paper_lens_count():
 
 def test_sizing_flow_chart():
     """Flow-chart sizing: P = 10 sqrt(kappa_*), I = (S + 2P)/|1 - kappa -+ gamma|,
-    widened to a whole number of rays of side sqrt(s^2 / N_av) (reading R3),
+    widened to a whole number of rays of side sqrt(s^2 / N_av), N_av per unlensed source pixel,
     centred on the image of the source centre."""
     p = oracle.make_params(0.45, 0.0, 0.45, (-10.0, 10.0, -10.0, 10.0), 2000, 100.0)
     q = oracle.size(p)
