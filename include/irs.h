@@ -75,7 +75,9 @@ typedef struct irs_params {
   int32_t window;         /* INTERP: cells within this Chebyshev distance sum lenses directly into
                              the series; 0 = default */
   int32_t kernel_variant; /* INTERP: ray-pass variant 0..9 (rays per thread, level-2 sub-cells,
-                             sub-cell terms, CTAs per SM, binning); irs_autotune picks one */
+                             sub-cell terms, CTAs per SM, binning, shared reciprocals);
+                             irs_autotune picks one.  BRUTE: variant 0..9 (rows per thread,
+                             rows sharing a reciprocal, packed FP32x2 rows); 0 = default */
   int32_t reserved[6];    /* must be 0 */
 } irs_params;
 
