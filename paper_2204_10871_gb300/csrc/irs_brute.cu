@@ -182,8 +182,8 @@ enum { MODE_MAP = 0, MODE_DUMP = 1 };
 // 1e5-lens band against 58.1 % for variant 1, the fastest scalar form.
 #define BR_VARIANTS(X)                                                                         \
   X(0, 16, 4, 1, 512) X(1, 16, 8, 0, 512) X(2, 8, 4, 0, 512) X(3, 8, 2, 0, 512)                 \
-  X(4, 16, 4, 0, 512) X(5, 16, 2, 0, 512) X(6, 16, 8, 1, 512) X(7, 8, 4, 1, 768)                \
-  X(8, 8, 2, 1, 768) X(9, 8, 0, 1, 768)
+  X(4, 16, 4, 0, 512) X(5, 16, 2, 0, 512) X(6, 16, 8, 1, 512) X(7, 16, 6, 1, 512)                \
+  X(8, 16, 2, 1, 512) X(9, 16, 4, 1, 640)
 constexpr int BR_NVARIANT = 10;
 
 template <int MODE, int R, int PAIRED, int PACK, int TPSM>
