@@ -283,12 +283,36 @@ __global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, double2* __restr
   for (int k = 0; k < IP_P; ++k) spec[(int64_t)k * G + f] = make_double2(Cc[k].re, Cc[k].im);
 }
 
+// Series terms of the per-cell finalize accumulated in FP64; the others in
+// FP32.  A window lens sits >= 1.5 cells from the cell centre and a ray
+// <= 0.71 cells from it, so term k of a lens contributes at most
+// (m/d) 0.47^k: FP32 rounding of the terms k >= 3 moves a ray's deflection by
+// <= 1e-7 x 0.1 of that lens's field, and every term k >= 1 is stored as FP32
+// for the ray pass anyway.  Terms 0..2 (the constant, which sets the ray's
+// beta, and the two largest slopes) keep FP64.
+constexpr int FIN_K64 = 3;
+constexpr int FIN_K32 = IP_KMAX - FIN_K64;
+
+// 1/a for complex a, |a| >~ 1e-19 (cell or theta_E units): an FP32 seed for
+// 1/|a|^2 refined by one FP64 Newton step (relative error ~1e-14), instead of
+// two FP64 divisions.
+__device__ __forceinline__ cd crecip_nr(cd a) {
+  const double q = a.re * a.re + a.im * a.im;
+  double r = (double)rcp_approx((float)q);
+  r = r * fma(-q, r, 2.0);
+  return {a.re * r, -a.im * r};
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
 // Per ray cell of [rc0, rc1): window P2L, M2L result, sheet series, centre
 // term, base pixel.
-__global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
-                              const int32_t* __restrict__ start, const double2* __restrict__ pos,
-                              const double* __restrict__ m, const double2* __restrict__ conv, MlpFar far,
-                              CellRec* __restrict__ recs, float2* __restrict__ coef, int64_t rc0, int64_t rc1) {
+__global__ void __launch_bounds__(64)
+k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* __restrict__ start,
+              const double2* __restrict__ pos, const double* __restrict__ m, const double2* __restrict__ conv,
+              MlpFar far, CellRec* __restrict__ recs, float2* __restrict__ coef, int64_t rc0, int64_t rc1) {
   const int64_t rc = rc0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (rc >= rc1) return;
   const int cx = (int)(rc % ig.nrcx) + ig.ox, cy = (int)(rc / ig.nrcx) + ig.oy;
@@ -298,8 +322,14 @@ __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
   const double h = ig.h, inv_h = 1.0 / h;
   const int K = ig.K;
 
-  cd acc[IP_KMAX];  // coefficients of tau^k before the 1/h of the lens parts
-  for (int k = 0; k < K; ++k) acc[k] = {0.0, 0.0};
+  // coefficients of tau^k before the 1/h of the lens parts: k < FIN_K64 in
+  // FP64, the rest in FP32 (terms past K are computed and dropped)
+  cd acc[FIN_K64];
+  float2 accf[FIN_K32];
+#pragma unroll
+  for (int k = 0; k < FIN_K64; ++k) acc[k] = {0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < FIN_K32; ++k) accf[k] = make_float2(0.f, 0.f);
   // direct ring: lenses of cells at Chebyshev distance 2..W (series mode), or
   // every lens outside the near block weighted by w(r) out to R_f (network mode)
   const int Wd = far.active ? (int)ceil(far.rf) + 1 : ig.W;
@@ -318,36 +348,66 @@ __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
           wm *= mlp_ring_weight(hypot(d.re, d.im), far.rf);
           if (wm == 0.0) continue;
         }
-        const cd inv = crecip(d);
-        cd pw = {wm * inv.re, wm * inv.im};
-        for (int k = 0; k < K; ++k) {  // + m d^-(k+1)
+        const cd inv = crecip_nr(d);
+        cd pw = {wm * inv.re, wm * inv.im};  // + m d^-(k+1)
+#pragma unroll
+        for (int k = 0; k < FIN_K64; ++k) {
           acc[k].re += pw.re;
           acc[k].im += pw.im;
           pw = cmul(pw, inv);
+        }
+        const float2 invf = make_float2((float)inv.re, (float)inv.im);
+        float2 pf = make_float2((float)pw.re, (float)pw.im);
+#pragma unroll
+        for (int k = 0; k < FIN_K32; ++k) {
+          accf[k].x += pf.x;
+          accf[k].y += pf.y;
+          pf = cmulf(pf, invf);
         }
       }
     }
   }
   // outer cells through the FFT convolution (series mode)
   if (!far.active) {
-    for (int k = 0; k < IP_P && k < K; ++k) {
+#pragma unroll
+    for (int k = 0; k < IP_P; ++k) {
+      if (k >= K) break;
       const double2 v = conv[(int64_t)k * ncells + c];
-      acc[k].re += v.x;
-      acc[k].im += v.y;
+      if (k < FIN_K64) {
+        acc[k].re += v.x;
+        acc[k].im += v.y;
+      } else {
+        accf[k - FIN_K64].x += (float)v.x;
+        accf[k - FIN_K64].y += (float)v.y;
+      }
     }
   }
-  for (int k = 0; k < K; ++k) {
+#pragma unroll
+  for (int k = 0; k < FIN_K64; ++k) {
     acc[k].re *= inv_h;
     acc[k].im *= inv_h;
+  }
+  const float inv_hf = (float)inv_h;
+#pragma unroll
+  for (int k = 0; k < FIN_K32; ++k) {
+    accf[k].x *= inv_hf;
+    accf[k].y *= inv_hf;
   }
   // network mode away from corners: G = -L_ring - U - kappa_* conj(z_C); the
   // sheet's g cancels against the definition of U
   const bool learned = far.active && far.corner[rc] < 0;
   if (far.active && !learned) {  // corner zone: exact far-far sum, then the sheet as usual
     const double2* ex = far.exact + (int64_t)far.corner[rc] * MLP_KEXACT;
-    for (int k = 0; k < MLP_KEXACT && k < K; ++k) {
-      acc[k].re -= ex[k].x;
-      acc[k].im -= ex[k].y;
+#pragma unroll
+    for (int k = 0; k < MLP_KEXACT; ++k) {
+      if (k >= K) break;
+      if (k < FIN_K64) {
+        acc[k].re -= ex[k].x;
+        acc[k].im -= ex[k].y;
+      } else {
+        accf[k - FIN_K64].x -= (float)ex[k].x;
+        accf[k - FIN_K64].y -= (float)ex[k].y;
+      }
     }
   }
 
@@ -360,10 +420,17 @@ __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
   cd B;
   if (learned) {
     const double ks0 = g.kstar_scale * msum[0];
-    for (int k = 0; k < MLP_KFF && k < K; ++k) {
+#pragma unroll
+    for (int k = 0; k < MLP_KFF; ++k) {
+      if (k >= K) break;
       const float2 u = far.U[rc * MLP_KFF + k];
-      acc[k].re -= (double)u.x;
-      acc[k].im -= (double)u.y;
+      if (k < FIN_K64) {
+        acc[k].re -= (double)u.x;
+        acc[k].im -= (double)u.y;
+      } else {
+        accf[k - FIN_K64].x -= u.x;
+        accf[k - FIN_K64].y -= u.y;
+      }
     }
     acc[0].re -= ks0 * zx;  // kappa_* conj(z_C)
     acc[0].im += ks0 * zy;
@@ -403,14 +470,23 @@ __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
       acc[0].im -= ac * wl.re;
       acc[1].re += ac * L.im * h;
       acc[1].im -= ac * (L.re + 1.0) * h;
-      const cd inv = crecip(w);
-      cd pw = {inv.re * h * h, inv.im * h * h};  // h^n / w^(n-1) at n = 2
+      const cd inv = crecip_nr(w);
       const cd ih = {inv.re * h, inv.im * h};
-      for (int n = 2; n < K; ++n) {
-        const double cf = ((n & 1) ? -1.0 : 1.0) / (double)(n * (n - 1));
-        acc[n].re += ac * cf * pw.im;
-        acc[n].im -= ac * cf * pw.re;
-        pw = cmul(pw, ih);
+      cd pw = {inv.re * h * h, inv.im * h * h};  // h^n / w^(n-1) at n = 2
+      // n = 2 in FP64 (FIN_K64 = 3), n >= 3 in FP32
+      acc[2].re += ac * 0.5 * pw.im;
+      acc[2].im -= ac * 0.5 * pw.re;
+      pw = cmul(pw, ih);
+      const float2 ihf = make_float2((float)ih.re, (float)ih.im);
+      float2 pf = make_float2((float)pw.re, (float)pw.im);
+      const float acf = (float)ac;
+#pragma unroll
+      for (int k = 0; k < FIN_K32; ++k) {
+        const int n = k + FIN_K64;
+        const float cf = ((n & 1) ? -1.0f : 1.0f) / (float)(n * (n - 1));
+        accf[k].x += acf * cf * pf.y;
+        accf[k].y -= acf * cf * pf.x;
+        pf = cmulf(pf, ihf);
       }
     }
     B = {(1.0 - g.kappa_s - g.gamma) * zx, -(1.0 - g.kappa_s + g.gamma) * zy};
@@ -426,7 +502,11 @@ __global__ void k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum,
   split_df(B.re - (g.src_x0 + fx * g.sx), r.bx_hi, r.bx_lo);
   split_df(-B.im - (g.src_y0 + fy * g.sy), r.by_hi, r.by_lo);
   recs[rc] = r;
-  for (int k = 0; k < K; ++k) coef[rc * K + k] = make_float2((float)acc[k].re, (float)acc[k].im);
+#pragma unroll
+  for (int k = 0; k < IP_KMAX; ++k) {
+    if (k >= K) break;
+    coef[rc * K + k] = k < FIN_K64 ? make_float2((float)acc[k].re, (float)acc[k].im) : accf[k - FIN_K64];
+  }
 }
 
 // ------------------------------------------------------------ ray pass
