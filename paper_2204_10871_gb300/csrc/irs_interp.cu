@@ -41,7 +41,9 @@ namespace irs {
 namespace {
 
 constexpr int IP_KMAX = 32;        // local series terms (max)
-constexpr int IP_P = 18;           // multipole terms and local terms produced by the M2L
+constexpr int IP_P = 18;           // multipole terms per cell
+constexpr int IP_KF = 14;          // local terms produced by the M2L (cells >= 4 apart:
+                                   // truncation (0.71 / 3.29)^14 ~ 5e-10 of a cell's field)
 constexpr int IP_NEAR_MAX = 1024;  // lenses of a 3x3 block held in shared memory
 constexpr int IP_KMAX_RAYS = 1024;  // rays along a cell side (row table in shared memory)
 constexpr int IP_THREADS = 256;
@@ -231,8 +233,9 @@ __global__ void k_ip_p2m(IpGeo ig, const int32_t* __restrict__ start, const doub
   for (int j = 0; j < IP_P; ++j) mpole[(int64_t)j * ncells + c] = make_double2(a[j].re, a[j].im);
 }
 
-// Translation kernels on the padded grid: K'_n[e] = (-e)^-(n+1) for offsets
-// e (cell units, wrapped) with Chebyshev norm > W, else 0.
+// Translation kernels on the padded grid, scaled by n!:
+// K'_n[e] = n! (-e)^-(n+1) for offsets e (cell units, wrapped) with Chebyshev
+// norm > W, else 0 (the n! is one factor of the M2L's binomial, below).
 __global__ void k_ip_kernel_grid(int Nx, int Ny, int W, int nker, double2* __restrict__ kg) {
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t G = (int64_t)Nx * Ny;
@@ -243,44 +246,51 @@ __global__ void k_ip_kernel_grid(int Nx, int Ny, int W, int nker, double2* __res
   cd inv = {0.0, 0.0};
   if (far) inv = crecip(cd{-(double)sx, -(double)sy});
   cd pw = inv;
+  double fact = 1.0;  // n!
   for (int n = 0; n < nker; ++n) {
-    kg[(int64_t)n * G + f] = far ? make_double2(pw.re, pw.im) : make_double2(0.0, 0.0);
+    if (n > 0) fact *= (double)n;
+    kg[(int64_t)n * G + f] = far ? make_double2(pw.re * fact, pw.im * fact) : make_double2(0.0, 0.0);
     pw = cmul(pw, inv);
   }
 }
 
 // Pointwise M2L in frequency space:
-//   C_k = sum_j (-1)^j binom(j+k, k) A_j Kh_{j+k},  j, k < P
+//   C_k = sum_j (-1)^j binom(j+k, k) A_j Kh_{j+k},  j < P, k < KF,
+// with binom(j+k, k) = (j+k)! / (j! k!): the (j+k)! sits in the kernel
+// spectra, so each term is one complex multiply-add of (-1)^j A_j / j! and
+// the scaled kernel, and C_k takes the 1/k! at the end.
 __global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, double2* __restrict__ spec,
                                                      const double2* __restrict__ kspec) {
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= G) return;
-  cd A[IP_P], Cc[IP_P];
+  cd A[IP_P], Cc[IP_KF];
+  double ifact = 1.0;  // 1/j!, folded at compile time
 #pragma unroll
   for (int j = 0; j < IP_P; ++j) {
+    if (j > 0) ifact /= (double)j;
     const double2 v = spec[(int64_t)j * G + f];
-    const double sgn = (j & 1) ? -1.0 : 1.0;
-    A[j] = {sgn * v.x, sgn * v.y};
-    Cc[j] = {0.0, 0.0};
+    const double sc = ((j & 1) ? -1.0 : 1.0) * ifact;
+    A[j] = {sc * v.x, sc * v.y};
   }
 #pragma unroll
-  for (int nn = 0; nn < 2 * IP_P - 1; ++nn) {
+  for (int k = 0; k < IP_KF; ++k) Cc[k] = {0.0, 0.0};
+#pragma unroll
+  for (int nn = 0; nn < IP_P + IP_KF - 1; ++nn) {
     const double2 kv = kspec[(int64_t)nn * G + f];
 #pragma unroll
     for (int j = 0; j < IP_P; ++j) {
       const int k = nn - j;
-      if (k < 0 || k >= IP_P) continue;
-      // binom(j + k, k) = binom(nn, k), folded at compile time
-      double b = 1.0;
-#pragma unroll
-      for (int q = 1; q <= k; ++q) b = b * (double)(nn - k + q) / (double)q;
-      const double tr = A[j].re * kv.x - A[j].im * kv.y, ti = A[j].re * kv.y + A[j].im * kv.x;
-      Cc[k].re += b * tr;
-      Cc[k].im += b * ti;
+      if (k < 0 || k >= IP_KF) continue;
+      Cc[k].re = fma(A[j].re, kv.x, fma(-A[j].im, kv.y, Cc[k].re));
+      Cc[k].im = fma(A[j].re, kv.y, fma(A[j].im, kv.x, Cc[k].im));
     }
   }
+  double kfact = 1.0;  // 1/k!
 #pragma unroll
-  for (int k = 0; k < IP_P; ++k) spec[(int64_t)k * G + f] = make_double2(Cc[k].re, Cc[k].im);
+  for (int k = 0; k < IP_KF; ++k) {
+    if (k > 0) kfact /= (double)k;
+    spec[(int64_t)k * G + f] = make_double2(Cc[k].re * kfact, Cc[k].im * kfact);
+  }
 }
 
 // Series terms of the per-cell finalize accumulated in FP64; the others in
@@ -370,7 +380,7 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
   // outer cells through the FFT convolution (series mode)
   if (!far.active) {
 #pragma unroll
-    for (int k = 0; k < IP_P; ++k) {
+    for (int k = 0; k < IP_KF; ++k) {
       if (k >= K) break;
       const double2 v = conv[(int64_t)k * ncells + c];
       if (k < FIN_K64) {
@@ -1083,7 +1093,7 @@ irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* ma
     const int64_t G = (int64_t)S->fft.Nx * S->fft.Ny;
     k_ip_m2l_freq<<<(unsigned)((G + 127) / 128), 128, 0, s>>>(G, S->spec, S->kspec);
     IP_TRY(cudaGetLastError());
-    IP_TRY(fft2d_inverse(S->spec, S->fft, ig.ncx, ig.ncy, S->conv, ncells, ig.P, s));
+    IP_TRY(fft2d_inverse(S->spec, S->fft, ig.ncx, ig.ncy, S->conv, ncells, IP_KF, s));
   }
   const int64_t nrc = (int64_t)ig.nrcx * ig.nrcy;
   if (rc1 < 0 || rc1 > nrc) rc1 = nrc;
@@ -1181,8 +1191,8 @@ irs_status interp_plan(irs_plan_t* P) {
   const size_t o_cnt = take(sizeof(int32_t) * ncells), o_start = take(sizeof(int32_t) * (ncells + 1));
   const size_t o_cur = take(sizeof(int32_t) * ncells);
   const size_t o_sb = take(sizeof(int32_t) * ((ncells + SCAN_B - 1) / SCAN_B + 1));
-  const size_t o_mp = take(sizeof(double2) * ig.P * ncells), o_conv = take(sizeof(double2) * ig.P * ncells);
-  const size_t o_spec = take(sizeof(double2) * ig.P * G), o_kspec = take(sizeof(double2) * (2 * ig.P - 1) * G);
+  const size_t o_mp = take(sizeof(double2) * ig.P * ncells), o_conv = take(sizeof(double2) * IP_KF * ncells);
+  const size_t o_spec = take(sizeof(double2) * ig.P * G), o_kspec = take(sizeof(double2) * (ig.P + IP_KF - 1) * G);
   const size_t o_rec = take(sizeof(CellRec) * nrc), o_coef = take(sizeof(float2) * ig.K * nrc);
   if (cudaMalloc(&S->ws, off) != cudaSuccess) {
     cudaGetLastError();
@@ -1204,7 +1214,7 @@ irs_status interp_plan(irs_plan_t* P) {
   irs_status st = alloc_lens_buffers(S, nstar + nstar / 4 + 256);
   if (st != IRS_OK) return st;
   // translation kernels and their spectra, once per plan
-  const int nker = 2 * ig.P - 1;
+  const int nker = ig.P + IP_KF - 1;
   k_ip_kernel_grid<<<(unsigned)((G + 255) / 256), 256>>>(f.Nx, f.Ny, ig.W, nker, S->kspec);
   if (cudaGetLastError() != cudaSuccess) return IRS_ERR_CUDA;
   if (fft2d_forward(S->kspec, f.Nx, f.Ny, G, S->kspec, f, nker, 0) != cudaSuccess) return IRS_ERR_CUDA;
