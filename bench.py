@@ -233,6 +233,8 @@ def run_ours(args):
     tune = None
     if args.variant >= 0:
         params.kernel_variant = args.variant
+        if args.cell_mult > 0:
+            params.cell_mult = args.cell_mult
     elif args.method == "interp" and not args.no_tune:  # untimed: pick cell size and ray-pass variant
         t0 = time.perf_counter()
         params, res = irs.irs_autotune(params, dxy, dm)
@@ -826,6 +828,7 @@ def main():
     ap.add_argument("--no-brute", action="store_true", help="skip the brute-force band")
     ap.add_argument("--no-tune", action="store_true", help="paper-rule cells, default ray pass")
     ap.add_argument("--variant", type=int, default=-1, help="fixed kernel variant (skips tuning)")
+    ap.add_argument("--cell-mult", type=float, default=0.0, help="with --variant: level-1 cell multiplier")
     ap.add_argument("--workload", default="", choices=["", "paper-mid", "high-res", "learned"],
                     help="default: paper-mid (learned for --method mlp)")
     ap.add_argument("--band-rows", type=int, default=0, help="brute band height (rows)")

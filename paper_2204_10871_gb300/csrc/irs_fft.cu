@@ -1,9 +1,11 @@
-// irs_fft.cu -- FP64 complex 2-D FFTs of power-of-two size for the far-field
+// irs_fft.cu -- FP64 complex 2-D FFTs of length 2^a 3^b for the far-field
 // convolution on the level-1 cell grid.
 //
-// A CTA loads B lines of length L (B*L <= 8192 complex doubles, 128 KB) into
-// shared memory in bit-reversed order, runs log2(L) radix-2 butterfly stages
-// with a twiddle table staged beside them, and writes the lines back.  Rows
+// A CTA loads B lines of length L = 3^n3 2^n2 (B*L <= 9216 complex doubles,
+// 144 KB) into shared memory in mixed-radix digit-reversed order, runs n3
+// radix-3 then n2 radix-2 in-place decimation-in-time stages with a twiddle
+// table W_L^t (t < L/2; W_L^(t + L/2) = -W_L^t) staged beside them, and writes
+// the lines back.  Rows
 // are contiguous lines; columns are strided lines, loaded B adjacent columns
 // at a time so that each row segment is one coalesced 16*B-byte access.
 // Zero padding is implicit: input elements at or beyond `in_len` read as 0,
@@ -22,7 +24,27 @@ __device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
+// Where input element e goes for the in-place decimation-in-time stages (n3
+// radix-3 stages, then n2 radix-2): the n2 low bits of e reversed, times 3^n3,
+// plus the n3 base-3 digits of e >> n2 reversed.  (For n3 = 0 this is the
+// bit reversal; for n3 > 0 the permutation is not its own inverse.)
+__device__ __forceinline__ unsigned digit_pos(unsigned e, int n3, int n2, unsigned pow3) {
+  const unsigned lo = e & ((1u << n2) - 1u);
+  unsigned hi = e >> n2, r3 = 0;
+  for (int i = 0; i < n3; ++i) {
+    const unsigned q = hi / 3u;
+    r3 = r3 * 3u + (hi - 3u * q);
+    hi = q;
+  }
+  return r3 + pow3 * (n2 > 0 ? (__brev(lo) >> (32 - n2)) : 0u);
+}
+
+// W_L^t for 0 <= t < L from the half table
+__device__ __forceinline__ double2 tw_at(const double2* w, int t, int half) {
+  if (t < half) return w[t];
+  const double2 v = w[t - half];
+  return make_double2(-v.x, -v.y);
+}
 
 template <bool INV>
 __global__ void __launch_bounds__(512) k_fft_lines(const double2* in, double2* out,
@@ -30,13 +52,15 @@ __global__ void __launch_bounds__(512) k_fft_lines(const double2* in, double2* o
   extern __shared__ double2 sm[];
   double2* x = sm;                           // [B][L]
   double2* w = sm + (size_t)d.B * d.L;       // [L/2]
-  const int L = d.L, B = d.B, logL = d.logL;
+  const int L = d.L, B = d.B, n3 = d.n3, n2 = d.n2, half_L = L / 2;
+  unsigned pow3 = 1;
+  for (int i = 0; i < n3; ++i) pow3 *= 3u;
   const int64_t line0 = (int64_t)blockIdx.x * B;
   const int64_t goff_in = (int64_t)blockIdx.y * d.in_grid_stride;
   const int64_t goff_out = (int64_t)blockIdx.y * d.out_grid_stride;
   const int nthr = blockDim.x;
   for (int k = threadIdx.x; k < L / 2; k += nthr) w[k] = tw[k];
-  // load, bit-reversed
+  // load, digit-reversed
   for (int idx = threadIdx.x; idx < B * L; idx += nthr) {
     int b, e;
     if (d.in_elem_stride == 1) {
@@ -50,16 +74,43 @@ __global__ void __launch_bounds__(512) k_fft_lines(const double2* in, double2* o
     double2 v = make_double2(0.0, 0.0);
     if (line < d.n_lines && e < d.in_len)
       v = in[goff_in + line * d.in_line_stride + (int64_t)e * d.in_elem_stride];
-    x[b * L + bitrev((unsigned)e, logL)] = v;
+    x[b * L + digit_pos((unsigned)e, n3, n2, pow3)] = v;
   }
   __syncthreads();
-  for (int s = 1; s <= logL; ++s) {
-    const int half = 1 << (s - 1);
+  int m_prev = 1;  // span of the sub-transforms done so far
+  // radix-3 stages: y_q = sum_r (W_m^(j r) x_r) W_3^(q r)
+  const double s3 = INV ? -0.86602540378443864676 : 0.86602540378443864676;  // sqrt(3)/2
+  for (int s = 0; s < n3; ++s) {
+    const int m = m_prev * 3, stride = L / m;
+    for (int t = threadIdx.x; t < B * (L / 3); t += nthr) {
+      const int b = t / (L / 3), k = t % (L / 3);
+      const int j = k % m_prev;
+      const int i0 = (k / m_prev) * m + j, i1 = i0 + m_prev, i2 = i1 + m_prev;
+      double2 w1 = tw_at(w, j * stride, half_L), w2 = tw_at(w, 2 * j * stride, half_L);
+      if (INV) {
+        w1.y = -w1.y;
+        w2.y = -w2.y;
+      }
+      const double2 a = x[b * L + i0];
+      const double2 p = cmul2(x[b * L + i1], w1), q = cmul2(x[b * L + i2], w2);
+      const double2 t1 = make_double2(p.x + q.x, p.y + q.y);
+      const double2 t2 = make_double2(a.x - 0.5 * t1.x, a.y - 0.5 * t1.y);
+      const double2 dd = make_double2(p.x - q.x, p.y - q.y);
+      x[b * L + i0] = make_double2(a.x + t1.x, a.y + t1.y);
+      x[b * L + i1] = make_double2(t2.x + s3 * dd.y, t2.y - s3 * dd.x);
+      x[b * L + i2] = make_double2(t2.x - s3 * dd.y, t2.y + s3 * dd.x);
+    }
+    __syncthreads();
+    m_prev = m;
+  }
+  // radix-2 stages
+  for (int s = 0; s < n2; ++s) {
+    const int m = m_prev * 2, stride = L / m;
     for (int t = threadIdx.x; t < B * (L / 2); t += nthr) {
       const int b = t / (L / 2), k = t % (L / 2);
-      const int j = k & (half - 1);
-      const int i0 = ((k >> (s - 1)) << s) + j, i1 = i0 + half;
-      double2 tw_ = w[j << (logL - s)];
+      const int j = k % m_prev;
+      const int i0 = (k / m_prev) * m + j, i1 = i0 + m_prev;
+      double2 tw_ = w[j * stride];
       if (INV) tw_.y = -tw_.y;
       const double2 u = x[b * L + i0];
       const double2 v = cmul2(x[b * L + i1], tw_);
@@ -67,6 +118,7 @@ __global__ void __launch_bounds__(512) k_fft_lines(const double2* in, double2* o
       x[b * L + i1] = make_double2(u.x - v.x, u.y - v.y);
     }
     __syncthreads();
+    m_prev = m;
   }
   for (int idx = threadIdx.x; idx < B * L; idx += nthr) {
     int b, e;
@@ -89,10 +141,27 @@ __global__ void __launch_bounds__(512) k_fft_lines(const double2* in, double2* o
 
 }  // namespace
 
-int ilog2_exact(int64_t n) {
-  int l = 0;
-  while (((int64_t)1 << l) < n) ++l;
-  return ((int64_t)1 << l) == n ? l : -1;
+int fft_good_size(int64_t n_min, int* n3, int* n2) {
+  int64_t best = -1;
+  int b3 = 0, b2 = 0;
+  int64_t p3 = 1;
+  for (int i3 = 0; p3 <= FFT_MAX_LEN; ++i3, p3 *= 3) {
+    int64_t v = p3 * 2;
+    int i2 = 1;
+    while (v < n_min) {
+      v *= 2;
+      ++i2;
+    }
+    if (v <= FFT_MAX_LEN && (best < 0 || v < best)) {
+      best = v;
+      b3 = i3;
+      b2 = i2;
+    }
+  }
+  if (best < 0) return -1;
+  *n3 = b3;
+  *n2 = b2;
+  return (int)best;
 }
 
 cudaError_t fft_twiddles(int L, double2** d_tw) {
@@ -127,7 +196,7 @@ cudaError_t fft_lines(const double2* in, double2* out, FftLines d, int ngrids, c
   return cudaGetLastError();
 }
 
-// Lines per CTA for a line length L: fill the 8192-element shared buffer.
+// Lines per CTA for a line length L: fill the shared line buffer.
 static int lines_per_cta(int L) {
   int B = FFT_MAX_ELEMS / L;
   return B < 1 ? 1 : (B > 16 ? 16 : B);
@@ -137,7 +206,7 @@ cudaError_t fft2d_forward(const double2* compact, int64_t nx, int64_t ny, int64_
                           double2* spec, const Fft2d& f, int ngrids, cudaStream_t s) {
   // rows: compact rows [0, ny) -> spectrum rows, zero-padded to Nx
   FftLines r{};
-  r.L = f.Nx; r.logL = f.logNx; r.B = lines_per_cta(f.Nx);
+  r.L = f.Nx; r.n3 = f.n3x; r.n2 = f.n2x; r.B = lines_per_cta(f.Nx);
   r.n_lines = ny; r.in_len = (int)nx; r.out_len = f.Nx;
   r.in_line_stride = nx; r.in_elem_stride = 1; r.out_line_stride = f.Nx; r.out_elem_stride = 1;
   r.in_grid_stride = in_grid_stride; r.out_grid_stride = (int64_t)f.Nx * f.Ny; r.scale = 1.0;
@@ -145,7 +214,7 @@ cudaError_t fft2d_forward(const double2* compact, int64_t nx, int64_t ny, int64_
   if (e != cudaSuccess) return e;
   // columns: all Nx, rows >= ny read as zero
   FftLines c{};
-  c.L = f.Ny; c.logL = f.logNy; c.B = lines_per_cta(f.Ny);
+  c.L = f.Ny; c.n3 = f.n3y; c.n2 = f.n2y; c.B = lines_per_cta(f.Ny);
   c.n_lines = f.Nx; c.in_len = (int)ny; c.out_len = f.Ny;
   c.in_line_stride = 1; c.in_elem_stride = f.Nx; c.out_line_stride = 1; c.out_elem_stride = f.Nx;
   c.in_grid_stride = (int64_t)f.Nx * f.Ny; c.out_grid_stride = (int64_t)f.Nx * f.Ny; c.scale = 1.0;
@@ -155,14 +224,14 @@ cudaError_t fft2d_forward(const double2* compact, int64_t nx, int64_t ny, int64_
 cudaError_t fft2d_inverse(double2* spec, const Fft2d& f, int64_t nx, int64_t ny, double2* compact,
                           int64_t out_grid_stride, int ngrids, cudaStream_t s) {
   FftLines c{};
-  c.L = f.Ny; c.logL = f.logNy; c.B = lines_per_cta(f.Ny);
+  c.L = f.Ny; c.n3 = f.n3y; c.n2 = f.n2y; c.B = lines_per_cta(f.Ny);
   c.n_lines = f.Nx; c.in_len = f.Ny; c.out_len = (int)ny;
   c.in_line_stride = 1; c.in_elem_stride = f.Nx; c.out_line_stride = 1; c.out_elem_stride = f.Nx;
   c.in_grid_stride = (int64_t)f.Nx * f.Ny; c.out_grid_stride = (int64_t)f.Nx * f.Ny; c.scale = 1.0;
   cudaError_t e = fft_lines(spec, spec, c, ngrids, f.tw_y, true, s);
   if (e != cudaSuccess) return e;
   FftLines r{};
-  r.L = f.Nx; r.logL = f.logNx; r.B = lines_per_cta(f.Nx);
+  r.L = f.Nx; r.n3 = f.n3x; r.n2 = f.n2x; r.B = lines_per_cta(f.Nx);
   r.n_lines = ny; r.in_len = f.Nx; r.out_len = (int)nx;
   r.in_line_stride = f.Nx; r.in_elem_stride = 1; r.out_line_stride = nx; r.out_elem_stride = 1;
   r.in_grid_stride = (int64_t)f.Nx * f.Ny; r.out_grid_stride = out_grid_stride;

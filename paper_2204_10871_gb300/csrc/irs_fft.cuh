@@ -1,4 +1,4 @@
-// irs_fft.cuh -- FP64 complex power-of-two FFTs in shared memory (irs_fft.cu).
+// irs_fft.cuh -- FP64 complex FFTs of length 2^a 3^b (a >= 1) in shared memory (irs_fft.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -6,12 +6,13 @@
 
 namespace irs {
 
-constexpr int FFT_MAX_ELEMS = 8192;  // complex doubles per CTA line buffer (128 KB)
-constexpr int FFT_MAX_LEN = 8192;    // longest line
+constexpr int FFT_MAX_ELEMS = 9216;  // complex doubles per CTA line buffer (144 KB; with the
+                                     // 72 KB twiddle table 216 KB of shared memory)
+constexpr int FFT_MAX_LEN = 9216;    // longest line (3^2 2^10)
 
 // One batched pass of 1-D FFTs over `n_lines` lines of length L.
 struct FftLines {
-  int L, logL, B;           // line length, log2 L, lines per CTA
+  int L, n3, n2, B;         // line length L = 3^n3 2^n2, lines per CTA
   int in_len, out_len;      // valid input elements (rest zero), outputs written
   int64_t n_lines;
   int64_t in_line_stride, in_elem_stride, out_line_stride, out_elem_stride;
@@ -21,12 +22,15 @@ struct FftLines {
 
 // A padded Nx x Ny spectrum layout with its twiddle tables.
 struct Fft2d {
-  int Nx, Ny, logNx, logNy;
+  int Nx, Ny;        // 3^n3 2^n2 each
+  int n3x, n2x, n3y, n2y;
   double2* tw_x;
   double2* tw_y;
 };
 
-int ilog2_exact(int64_t n);
+// Smallest length 2^a 3^b >= n_min with a >= 1 and at most FFT_MAX_LEN, or -1;
+// its radix-3 and radix-2 stage counts.
+int fft_good_size(int64_t n_min, int* n3, int* n2);
 cudaError_t fft_twiddles(int L, double2** d_tw);
 cudaError_t fft_setup_attributes();
 cudaError_t fft_lines(const double2* in, double2* out, FftLines d, int ngrids, const double2* tw,

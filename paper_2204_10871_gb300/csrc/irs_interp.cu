@@ -1002,12 +1002,6 @@ cudaError_t launch_ip_ray_batch(int variant, int64_t grid, cudaStream_t s, const
 }
 
 // ------------------------------------------------------------ host helpers
-int64_t next_pow2(int64_t n) {
-  int64_t p = 2;
-  while (p < n) p <<= 1;
-  return p;
-}
-
 irs_status alloc_lens_buffers(InterpState* S, int64_t cap) {
   if (S->lens_ws) cudaFree(S->lens_ws);
   S->lens_ws = nullptr;
@@ -1172,10 +1166,10 @@ irs_status interp_plan(irs_plan_t* P) {
   if (ig.W < 1) ig.W = 1;
 
   Fft2d& f = S->fft;
-  f.Nx = (int)next_pow2(2 * ncx - 1);
-  f.Ny = (int)next_pow2(2 * ncy - 1);
-  f.logNx = ilog2_exact(f.Nx);
-  f.logNy = ilog2_exact(f.Ny);
+  // padded lengths >= 2n - 1 (linear convolution), of the form 2^a 3^b
+  f.Nx = fft_good_size(2 * ncx - 1, &f.n3x, &f.n2x);
+  f.Ny = fft_good_size(2 * ncy - 1, &f.n3y, &f.n2y);
+  if (f.Nx < 0 || f.Ny < 0) return IRS_ERR_OVERFLOW;
   if (fft_setup_attributes() != cudaSuccess) return IRS_ERR_CUDA;
   if (fft_twiddles(f.Nx, &f.tw_x) != cudaSuccess) return IRS_ERR_OOM;
   if (fft_twiddles(f.Ny, &f.tw_y) != cudaSuccess) return IRS_ERR_OOM;
