@@ -171,7 +171,8 @@ def ip_flops_fixed(variant):
 # dram__bytes_write.sum), valid only for the kernel build, workload and cell
 # size they were captured on: (workload, cell multiplier, variant) -> bytes.
 # Source: profiles/k_ip_ray_paper-mid-full.md.
-IP_TRAFFIC = {("paper-mid", 1.0, 7): 46.848768e6 + 11.264e3}
+IP_TRAFFIC = {("paper-mid", 1.0, 7): 46.848768e6 + 11.264e3,
+              ("paper-mid", 0.71, 9): 75.718144e6 + 1.016576e6}
 
 
 def mean_near_lenses(info, xy):
