@@ -539,16 +539,16 @@ struct IpRayArgs {
 
 // Kernel variants of the ray pass (the autotuner picks one per plan):
 // rays per thread R, level-2 sub-cells per side Q, sub-cell series terms K2.
-// Q = 8 with 8 terms and Q = 16 with 6 terms both truncate below 1e-8 of the
-// nearest far lens's field (sub-cell half-diagonal / distance to it: 0.083
-// and 0.042).
+// The truncation is (sub-cell half-diagonal / distance to the nearest far
+// lens)^K2 of that lens's field: Q = 8, 10, 12, 16 give ratios 0.083, 0.067,
+// 0.057, 0.042, so 8, 7, 6 and 6 terms stay at or below ~3e-8.
 // MINB: CTAs per SM the register budget is sized for; BIN: warp binning by
 // __match_any_sync (0) or by runs of equal pixels (1); NPR: how many of a
 // thread's R/2 row pairs share one reciprocal per lens, 1/(r_a^2 r_b^2) (the
 // near sum is bound by the MUFU's 16 reciprocals per SM per clock; a shared
 // reciprocal trades one MUFU op for FP32 work on a pipe that is half idle).
 #define IP_VARIANTS(X)                                                                       \
-  X(0, 8, 8, 8, 2, 0, 0) X(1, 8, 16, 6, 2, 0, 0) X(2, 8, 16, 6, 3, 0, 2)                       \
+  X(0, 8, 12, 6, 3, 0, 0) X(1, 8, 10, 7, 3, 0, 0) X(2, 8, 16, 6, 3, 0, 2)                       \
   X(3, 8, 16, 6, 3, 0, 4) X(4, 8, 16, 6, 2, 1, 0) X(5, 8, 16, 6, 3, 1, 0)                      \
   X(6, 8, 16, 6, 3, 1, 2) X(7, 8, 16, 6, 3, 0, 0) X(8, 4, 16, 6, 4, 0, 0)                      \
   X(9, 8, 8, 8, 3, 0, 0)
