@@ -22,7 +22,7 @@
 
 namespace {
 
-const double CELL_MULTS[] = {0.5, 0.70710678, 1.0, 1.41421356, 2.0};
+const double CELL_MULTS[] = {0.5, 0.6, 0.70710678, 0.85, 1.0, 1.2, 1.41421356, 2.0};
 constexpr int NVARIANT = 10;
 constexpr double BAND_RAYS = 2.0e9;
 std::mutex g_file_mu;
