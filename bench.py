@@ -172,7 +172,8 @@ def ip_flops_fixed(variant):
 # size they were captured on: (workload, cell multiplier, variant) -> bytes.
 # Source: profiles/k_ip_ray_paper-mid-full.md.
 IP_TRAFFIC = {("paper-mid", 1.0, 7): 46.848768e6 + 11.264e3,
-              ("paper-mid", 0.71, 9): 75.718144e6 + 1.016576e6}
+              ("paper-mid", 0.71, 9): 75.718144e6 + 1.016576e6,
+              ("paper-mid", 0.85, 0): 58.065152e6 + 57.088e3}
 
 
 def mean_near_lenses(info, xy):
