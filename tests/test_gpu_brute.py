@@ -78,6 +78,34 @@ def test_c1_sampled_deflection():
     assert np.mean(pg != po_pix) <= 2e-3
 
 
+BRUTE_VARIANTS = range(10)
+
+
+@pytest.mark.parametrize("variant", BRUTE_VARIANTS)
+def test_every_brute_variant_meets_the_bars(variant):
+    """Each kernel variant (rows per thread, rows sharing a reciprocal, packed
+    rows, occupancy) against the FP64 oracle: the map (misbinned rays) and the
+    sampled deflections, with 400 lenses so that several shared-memory stages
+    and their TwoSum folds are exercised."""
+    torch = require_gpu()
+    po, pl = params_pair(**C1, kernel_variant=variant)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 400, seed=5, kappa_star=0.3)
+    qo, co, mo, landed, cg, mg = _map_pair(torch, po, pl, xy, m)
+    bad = misbinned(co, cg)
+    assert bad <= MISBIN_TOL * landed, f"{bad} of {landed} rays binned differently"
+    rng = np.random.default_rng(3)
+    idx = rng.integers(0, qo.n_rays, 2000).astype(np.int64)
+    _, bo, _ = oracle.shoot_rays(po, qo, xy, m, idx)
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        beta, _ = plan.shoot_rays(dxy, dm, torch.from_numpy(idx).cuda())
+        plan.sync()
+    err = np.abs(beta.cpu().numpy() - bo).max(1)
+    far = nearest_lens_distance(xy, ray_positions(qo, idx)) > NEAR_LENS
+    assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
+
+
 @pytest.mark.parametrize("npix,nav,n", [((7, 5), 9.3, 1), ((33, 17), 3.0, 255), ((16, 16), 4.0, 257),
                                         ((1, 1), 2000.0, 3)])
 def test_ragged_sizes(npix, nav, n):
@@ -140,3 +168,7 @@ def test_bad_arguments_raise():
             irs.irs_make_map(plan.handle, buf[1:], m, counts)
         with pytest.raises(ValueError):
             irs.irs_make_map(plan.handle, xy.float(), m, counts)
+    for method, bad in ((irs.IRS_BRUTE, 10), (irs.IRS_BRUTE, -1), (irs.IRS_INTERP, 10)):
+        _, p = params_pair(**C1, method=method, kernel_variant=bad)
+        with pytest.raises(irs.IrsError):  # no such kernel variant
+            irs.Plan(p)
