@@ -1,28 +1,26 @@
-// irs_fft.cu -- FP64 complex 2-D FFTs of length 2^a 3^b for the far-field
-// convolution on the level-1 cell grid.
+// irs_fft.cu -- complex 2-D FFTs of length 2^a 3^b for the far-field
+// convolution on the level-1 cell grid, in double-float arithmetic
+// (irs_df.cuh: 48-bit significands on the FP32 pipes).
 //
-// A CTA loads B lines of length L = 3^n3 2^n2 (B*L <= 9216 complex doubles,
+// A CTA loads B lines of length L = 3^n3 2^n2 (B*L <= 9216 complex values,
 // 144 KB) into shared memory in mixed-radix digit-reversed order, runs n3
 // radix-3 then n2 radix-2 in-place decimation-in-time stages with a twiddle
 // table W_L^t (t < L/2; W_L^(t + L/2) = -W_L^t) staged beside them, and writes
-// the lines back.  Rows
-// are contiguous lines; columns are strided lines, loaded B adjacent columns
-// at a time so that each row segment is one coalesced 16*B-byte access.
-// Zero padding is implicit: input elements at or beyond `in_len` read as 0,
-// and only the first `out_len` outputs of a line are written.
+// the lines back.  Rows are contiguous lines; columns are strided lines, loaded
+// B adjacent columns at a time so that each row segment is one coalesced
+// 16*B-byte access.  Zero padding is implicit: input elements at or beyond
+// `in_len` read as 0, and only the first `out_len` outputs of a line are
+// written.
 #include <math.h>
 
 #include <vector>
 
+#include "irs_df.cuh"
 #include "irs_fft.cuh"
 
 namespace irs {
 
 namespace {
-
-__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
 
 // Where input element e goes for the in-place decimation-in-time stages (n3
 // radix-3 stages, then n2 radix-2): the n2 low bits of e reversed, times 3^n3,
@@ -39,19 +37,24 @@ __device__ __forceinline__ unsigned digit_pos(unsigned e, int n3, int n2, unsign
   return r3 + pow3 * (n2 > 0 ? (__brev(lo) >> (32 - n2)) : 0u);
 }
 
-// W_L^t for 0 <= t < L from the half table
-__device__ __forceinline__ double2 tw_at(const double2* w, int t, int half) {
-  if (t < half) return w[t];
-  const double2 v = w[t - half];
-  return make_double2(-v.x, -v.y);
+// W_L^t for 0 <= t < L from the half table, conjugated for the inverse
+template <bool INV>
+__device__ __forceinline__ float4 tw_at(const float4* w, int t, int half) {
+  float4 v = t < half ? w[t] : w[t - half];
+  if (t >= half) v = make_float4(-v.x, -v.y, -v.z, -v.w);
+  if (INV) {
+    v.z = -v.z;
+    v.w = -v.w;
+  }
+  return v;
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(512) k_fft_lines(const double2* in, double2* out,
-                                                   FftLines d, const double2* __restrict__ tw) {
-  extern __shared__ double2 sm[];
-  double2* x = sm;                           // [B][L]
-  double2* w = sm + (size_t)d.B * d.L;       // [L/2]
+__global__ void __launch_bounds__(512) k_fft_lines(const float4* in, float4* out, FftLines d,
+                                                   const float4* __restrict__ tw) {
+  extern __shared__ float4 sm[];
+  float4* x = sm;                           // [B][L]
+  float4* w = sm + (size_t)d.B * d.L;       // [L/2]
   const int L = d.L, B = d.B, n3 = d.n3, n2 = d.n2, half_L = L / 2;
   unsigned pow3 = 1;
   for (int i = 0; i < n3; ++i) pow3 *= 3u;
@@ -71,34 +74,33 @@ __global__ void __launch_bounds__(512) k_fft_lines(const double2* in, double2* o
       e = idx / B;
     }
     const int64_t line = line0 + b;
-    double2 v = make_double2(0.0, 0.0);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (line < d.n_lines && e < d.in_len)
       v = in[goff_in + line * d.in_line_stride + (int64_t)e * d.in_elem_stride];
     x[b * L + digit_pos((unsigned)e, n3, n2, pow3)] = v;
   }
   __syncthreads();
   int m_prev = 1;  // span of the sub-transforms done so far
-  // radix-3 stages: y_q = sum_r (W_m^(j r) x_r) W_3^(q r)
-  const double s3 = INV ? -0.86602540378443864676 : 0.86602540378443864676;  // sqrt(3)/2
+  // radix-3 stages: y_q = sum_r (W_m^(j r) x_r) W_3^(q r);
+  // W_3 = -1/2 -+ i sqrt(3)/2, the halving is exact
+  const float2 s3 = INV ? make_float2(-8.660253882e-01f, -1.554362505e-08f)
+                        : make_float2(8.660253882e-01f, 1.554362505e-08f);  // sqrt(3)/2 = hi + lo
   for (int s = 0; s < n3; ++s) {
     const int m = m_prev * 3, stride = L / m;
     for (int t = threadIdx.x; t < B * (L / 3); t += nthr) {
       const int b = t / (L / 3), k = t % (L / 3);
       const int j = k % m_prev;
       const int i0 = (k / m_prev) * m + j, i1 = i0 + m_prev, i2 = i1 + m_prev;
-      double2 w1 = tw_at(w, j * stride, half_L), w2 = tw_at(w, 2 * j * stride, half_L);
-      if (INV) {
-        w1.y = -w1.y;
-        w2.y = -w2.y;
-      }
-      const double2 a = x[b * L + i0];
-      const double2 p = cmul2(x[b * L + i1], w1), q = cmul2(x[b * L + i2], w2);
-      const double2 t1 = make_double2(p.x + q.x, p.y + q.y);
-      const double2 t2 = make_double2(a.x - 0.5 * t1.x, a.y - 0.5 * t1.y);
-      const double2 dd = make_double2(p.x - q.x, p.y - q.y);
-      x[b * L + i0] = make_double2(a.x + t1.x, a.y + t1.y);
-      x[b * L + i1] = make_double2(t2.x + s3 * dd.y, t2.y - s3 * dd.x);
-      x[b * L + i2] = make_double2(t2.x - s3 * dd.y, t2.y + s3 * dd.x);
+      const float4 a = x[b * L + i0];
+      const float4 p = dfc_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
+      const float4 q = dfc_mul(x[b * L + i2], tw_at<INV>(w, 2 * j * stride, half_L));
+      const float4 t1 = dfc_add(p, q);
+      const float4 t2 = dfc_sub(a, make_float4(0.5f * t1.x, 0.5f * t1.y, 0.5f * t1.z, 0.5f * t1.w));
+      const float4 dd = dfc_sub(p, q);
+      const float2 u = df_mul(s3, dfc_im(dd)), v = df_mul(s3, dfc_re(dd));  // s3 Im(dd), s3 Re(dd)
+      x[b * L + i0] = dfc_add(a, t1);
+      x[b * L + i1] = dfc_make(df_add(dfc_re(t2), u), df_sub(dfc_im(t2), v));
+      x[b * L + i2] = dfc_make(df_sub(dfc_re(t2), u), df_add(dfc_im(t2), v));
     }
     __syncthreads();
     m_prev = m;
@@ -110,16 +112,16 @@ __global__ void __launch_bounds__(512) k_fft_lines(const double2* in, double2* o
       const int b = t / (L / 2), k = t % (L / 2);
       const int j = k % m_prev;
       const int i0 = (k / m_prev) * m + j, i1 = i0 + m_prev;
-      double2 tw_ = w[j * stride];
-      if (INV) tw_.y = -tw_.y;
-      const double2 u = x[b * L + i0];
-      const double2 v = cmul2(x[b * L + i1], tw_);
-      x[b * L + i0] = make_double2(u.x + v.x, u.y + v.y);
-      x[b * L + i1] = make_double2(u.x - v.x, u.y - v.y);
+      const float4 u = x[b * L + i0];
+      const float4 v = dfc_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
+      x[b * L + i0] = dfc_add(u, v);
+      x[b * L + i1] = dfc_sub(u, v);
     }
     __syncthreads();
     m_prev = m;
   }
+  const bool scaled = d.scale != 1.0;
+  const float2 sc = make_float2((float)d.scale, (float)(d.scale - (double)(float)d.scale));
   for (int idx = threadIdx.x; idx < B * L; idx += nthr) {
     int b, e;
     if (d.out_elem_stride == 1) {
@@ -131,9 +133,8 @@ __global__ void __launch_bounds__(512) k_fft_lines(const double2* in, double2* o
     }
     const int64_t line = line0 + b;
     if (line < d.n_lines && e < d.out_len) {
-      double2 v = x[b * L + e];
-      v.x *= d.scale;
-      v.y *= d.scale;
+      float4 v = x[b * L + e];
+      if (scaled) v = dfc_scale(v, sc);
       out[goff_out + line * d.out_line_stride + (int64_t)e * d.out_elem_stride] = v;
     }
   }
@@ -164,29 +165,29 @@ int fft_good_size(int64_t n_min, int* n3, int* n2) {
   return (int)best;
 }
 
-cudaError_t fft_twiddles(int L, double2** d_tw) {
-  std::vector<double2> h((size_t)(L / 2 > 0 ? L / 2 : 1));
+cudaError_t fft_twiddles(int L, float4** d_tw) {
+  std::vector<float4> h((size_t)(L / 2 > 0 ? L / 2 : 1));
   for (int k = 0; k < L / 2; ++k) {
     const double a = -2.0 * M_PI * (double)k / (double)L;
-    h[k] = make_double2(cos(a), sin(a));
+    h[k] = dfc_from_double(cos(a), sin(a));
   }
-  cudaError_t e = cudaMalloc(d_tw, h.size() * sizeof(double2));
+  cudaError_t e = cudaMalloc(d_tw, h.size() * sizeof(float4));
   if (e != cudaSuccess) return e;
-  return cudaMemcpy(*d_tw, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  return cudaMemcpy(*d_tw, h.data(), h.size() * sizeof(float4), cudaMemcpyHostToDevice);
 }
 
 cudaError_t fft_setup_attributes() {
-  const int max_smem = (int)(FFT_MAX_ELEMS * sizeof(double2) + FFT_MAX_LEN / 2 * sizeof(double2));
+  const int max_smem = (int)(FFT_MAX_ELEMS * sizeof(float4) + FFT_MAX_LEN / 2 * sizeof(float4));
   cudaError_t e = cudaFuncSetAttribute(k_fft_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_fft_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }
 
-cudaError_t fft_lines(const double2* in, double2* out, FftLines d, int ngrids, const double2* tw,
+cudaError_t fft_lines(const float4* in, float4* out, FftLines d, int ngrids, const float4* tw,
                       bool inverse, cudaStream_t s) {
   if (d.n_lines <= 0 || ngrids <= 0) return cudaSuccess;
   const int64_t blocks = (d.n_lines + d.B - 1) / d.B;
-  const size_t smem = (size_t)d.B * d.L * sizeof(double2) + (size_t)(d.L / 2) * sizeof(double2);
+  const size_t smem = (size_t)d.B * d.L * sizeof(float4) + (size_t)(d.L / 2) * sizeof(float4);
   const int threads = d.B * d.L / 2 >= 512 ? 512 : (d.B * d.L / 2 >= 32 ? d.B * d.L / 2 : 32);
   dim3 grid((unsigned)blocks, (unsigned)ngrids);
   if (inverse)
@@ -202,8 +203,8 @@ static int lines_per_cta(int L) {
   return B < 1 ? 1 : (B > 16 ? 16 : B);
 }
 
-cudaError_t fft2d_forward(const double2* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
-                          double2* spec, const Fft2d& f, int ngrids, cudaStream_t s) {
+cudaError_t fft2d_forward(const float4* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
+                          float4* spec, const Fft2d& f, int ngrids, cudaStream_t s) {
   // rows: compact rows [0, ny) -> spectrum rows, zero-padded to Nx
   FftLines r{};
   r.L = f.Nx; r.n3 = f.n3x; r.n2 = f.n2x; r.B = lines_per_cta(f.Nx);
@@ -221,7 +222,7 @@ cudaError_t fft2d_forward(const double2* compact, int64_t nx, int64_t ny, int64_
   return fft_lines(spec, spec, c, ngrids, f.tw_y, false, s);
 }
 
-cudaError_t fft2d_inverse(double2* spec, const Fft2d& f, int64_t nx, int64_t ny, double2* compact,
+cudaError_t fft2d_inverse(float4* spec, const Fft2d& f, int64_t nx, int64_t ny, float4* compact,
                           int64_t out_grid_stride, int ngrids, cudaStream_t s) {
   FftLines c{};
   c.L = f.Ny; c.n3 = f.n3y; c.n2 = f.n2y; c.B = lines_per_cta(f.Ny);
@@ -235,7 +236,7 @@ cudaError_t fft2d_inverse(double2* spec, const Fft2d& f, int64_t nx, int64_t ny,
   r.n_lines = ny; r.in_len = f.Nx; r.out_len = (int)nx;
   r.in_line_stride = f.Nx; r.in_elem_stride = 1; r.out_line_stride = nx; r.out_elem_stride = 1;
   r.in_grid_stride = (int64_t)f.Nx * f.Ny; r.out_grid_stride = out_grid_stride;
-  r.scale = 1.0 / ((double)f.Nx * (double)f.Ny);
+  r.scale = 1.0;
   return fft_lines(spec, compact, r, ngrids, f.tw_x, true, s);
 }
 

@@ -1,4 +1,6 @@
-// irs_fft.cuh -- FP64 complex FFTs of length 2^a 3^b (a >= 1) in shared memory (irs_fft.cu).
+// irs_fft.cuh -- complex double-float FFTs of length 2^a 3^b (a >= 1) in shared
+// memory (irs_fft.cu).  Values are float4 (re.hi, re.lo, im.hi, im.lo), see
+// irs_df.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -6,7 +8,7 @@
 
 namespace irs {
 
-constexpr int FFT_MAX_ELEMS = 9216;  // complex doubles per CTA line buffer (144 KB; with the
+constexpr int FFT_MAX_ELEMS = 9216;  // complex values per CTA line buffer (144 KB; with the
                                      // 72 KB twiddle table 216 KB of shared memory)
 constexpr int FFT_MAX_LEN = 9216;    // longest line (3^2 2^10)
 
@@ -17,29 +19,30 @@ struct FftLines {
   int64_t n_lines;
   int64_t in_line_stride, in_elem_stride, out_line_stride, out_elem_stride;
   int64_t in_grid_stride, out_grid_stride;  // between grids of a batch (gridDim.y)
-  double scale;
+  double scale;  // applied to the outputs (1: none)
 };
 
 // A padded Nx x Ny spectrum layout with its twiddle tables.
 struct Fft2d {
   int Nx, Ny;        // 3^n3 2^n2 each
   int n3x, n2x, n3y, n2y;
-  double2* tw_x;
-  double2* tw_y;
+  float4* tw_x;  // W_N^t, t < N/2, as double-float complex
+  float4* tw_y;
 };
 
 // Smallest length 2^a 3^b >= n_min with a >= 1 and at most FFT_MAX_LEN, or -1;
 // its radix-3 and radix-2 stage counts.
 int fft_good_size(int64_t n_min, int* n3, int* n2);
-cudaError_t fft_twiddles(int L, double2** d_tw);
+cudaError_t fft_twiddles(int L, float4** d_tw);
 cudaError_t fft_setup_attributes();
-cudaError_t fft_lines(const double2* in, double2* out, FftLines d, int ngrids, const double2* tw,
+cudaError_t fft_lines(const float4* in, float4* out, FftLines d, int ngrids, const float4* tw,
                       bool inverse, cudaStream_t s);
 // compact [ngrids][ny][nx] -> padded spectra [ngrids][Ny][Nx]
-cudaError_t fft2d_forward(const double2* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
-                          double2* spec, const Fft2d& f, int ngrids, cudaStream_t s);
-// padded spectra (overwritten) -> compact [ngrids][ny][nx], scaled by 1/(Nx Ny)
-cudaError_t fft2d_inverse(double2* spec, const Fft2d& f, int64_t nx, int64_t ny, double2* compact,
+cudaError_t fft2d_forward(const float4* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
+                          float4* spec, const Fft2d& f, int ngrids, cudaStream_t s);
+// padded spectra (overwritten) -> compact [ngrids][ny][nx], unnormalised (the
+// 1/(Nx Ny) is the caller's)
+cudaError_t fft2d_inverse(float4* spec, const Fft2d& f, int64_t nx, int64_t ny, float4* compact,
                           int64_t out_grid_stride, int ngrids, cudaStream_t s);
 
 }  // namespace irs

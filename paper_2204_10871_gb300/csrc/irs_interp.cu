@@ -32,6 +32,7 @@
 
 #include <new>
 
+#include "irs_df.cuh"
 #include "irs_fft.cuh"
 #include "irs_interp.cuh"
 #include "irs_mlp.cuh"
@@ -87,10 +88,11 @@ struct InterpState {
   float4* lens_rel;
   double2* lens_pos;
   double* lens_m;
-  double2* mpole;  // [P][ncells]
-  double2* spec;   // [P][Ny][Nx]
-  double2* kspec;  // [2P-1][Ny][Nx]
-  double2* conv;   // [P][ncells]
+  // far-field convolution, complex double-float (irs_df.cuh)
+  float4* mpole;  // [P][ncells]
+  float4* spec;   // [P][Ny][Nx]
+  float4* kspec;  // [P+KF-1][Ny][Nx], normalised by 1/(Nx Ny)
+  float4* conv;   // [KF][ncells]
   CellRec* recs;   // [nray cells]
   float2* coef;    // [nray cells][K]
   int grid_ray;
@@ -209,7 +211,7 @@ __global__ void k_ip_fill(IpGeo ig, const double2* __restrict__ xy, const double
 // ------------------------------------------------------------ far field
 // P2M: a_j = sum_i m_i ((z_i - z_S)/h)^j for the lenses of cell S.
 __global__ void k_ip_p2m(IpGeo ig, const int32_t* __restrict__ start, const double2* __restrict__ pos,
-                         const double* __restrict__ m, double2* __restrict__ mpole) {
+                         const double* __restrict__ m, float4* __restrict__ mpole) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ncells = (int64_t)ig.ncx * ig.ncy;
   if (c >= ncells) return;
@@ -230,13 +232,15 @@ __global__ void k_ip_p2m(IpGeo ig, const int32_t* __restrict__ start, const doub
     }
   }
 #pragma unroll
-  for (int j = 0; j < IP_P; ++j) mpole[(int64_t)j * ncells + c] = make_double2(a[j].re, a[j].im);
+  for (int j = 0; j < IP_P; ++j) mpole[(int64_t)j * ncells + c] = dfc_from_double(a[j].re, a[j].im);
 }
 
-// Translation kernels on the padded grid, scaled by n!:
-// K'_n[e] = n! (-e)^-(n+1) for offsets e (cell units, wrapped) with Chebyshev
-// norm > W, else 0 (the n! is one factor of the M2L's binomial, below).
-__global__ void k_ip_kernel_grid(int Nx, int Ny, int W, int nker, double2* __restrict__ kg) {
+// Translation kernels on the padded grid, scaled by n! / (Nx Ny):
+// K'_n[e] = n! (-e)^-(n+1) / (Nx Ny) for offsets e (cell units, wrapped) with
+// Chebyshev norm > W, else 0 (the n! is one factor of the M2L's binomial,
+// below; the 1/(Nx Ny) normalises the inverse FFT and keeps every spectrum
+// far inside the FP32 exponent range of the double-float convolution).
+__global__ void k_ip_kernel_grid(int Nx, int Ny, int W, int nker, float4* __restrict__ kg) {
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t G = (int64_t)Nx * Ny;
   if (f >= G) return;
@@ -246,50 +250,47 @@ __global__ void k_ip_kernel_grid(int Nx, int Ny, int W, int nker, double2* __res
   cd inv = {0.0, 0.0};
   if (far) inv = crecip(cd{-(double)sx, -(double)sy});
   cd pw = inv;
-  double fact = 1.0;  // n!
+  double fact = 1.0 / (double)G;  // n! / (Nx Ny)
   for (int n = 0; n < nker; ++n) {
     if (n > 0) fact *= (double)n;
-    kg[(int64_t)n * G + f] = far ? make_double2(pw.re * fact, pw.im * fact) : make_double2(0.0, 0.0);
+    kg[(int64_t)n * G + f] = far ? dfc_from_double(pw.re * fact, pw.im * fact) : make_float4(0.f, 0.f, 0.f, 0.f);
     pw = cmul(pw, inv);
   }
 }
 
-// Pointwise M2L in frequency space:
+// Pointwise M2L in frequency space, in double-float:
 //   C_k = sum_j (-1)^j binom(j+k, k) A_j Kh_{j+k},  j < P, k < KF,
 // with binom(j+k, k) = (j+k)! / (j! k!): the (j+k)! sits in the kernel
 // spectra, so each term is one complex multiply-add of (-1)^j A_j / j! and
 // the scaled kernel, and C_k takes the 1/k! at the end.
-__global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, double2* __restrict__ spec,
-                                                     const double2* __restrict__ kspec) {
+__global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, float4* __restrict__ spec,
+                                                     const float4* __restrict__ kspec) {
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= G) return;
-  cd A[IP_P], Cc[IP_KF];
+  float4 A[IP_P], Cc[IP_KF];
   double ifact = 1.0;  // 1/j!, folded at compile time
 #pragma unroll
   for (int j = 0; j < IP_P; ++j) {
     if (j > 0) ifact /= (double)j;
-    const double2 v = spec[(int64_t)j * G + f];
-    const double sc = ((j & 1) ? -1.0 : 1.0) * ifact;
-    A[j] = {sc * v.x, sc * v.y};
+    A[j] = dfc_scale(spec[(int64_t)j * G + f], df_from_double(((j & 1) ? -1.0 : 1.0) * ifact));
   }
 #pragma unroll
-  for (int k = 0; k < IP_KF; ++k) Cc[k] = {0.0, 0.0};
+  for (int k = 0; k < IP_KF; ++k) Cc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int nn = 0; nn < IP_P + IP_KF - 1; ++nn) {
-    const double2 kv = kspec[(int64_t)nn * G + f];
+    const float4 kv = kspec[(int64_t)nn * G + f];
 #pragma unroll
     for (int j = 0; j < IP_P; ++j) {
       const int k = nn - j;
       if (k < 0 || k >= IP_KF) continue;
-      Cc[k].re = fma(A[j].re, kv.x, fma(-A[j].im, kv.y, Cc[k].re));
-      Cc[k].im = fma(A[j].re, kv.y, fma(A[j].im, kv.x, Cc[k].im));
+      Cc[k] = dfc_add(Cc[k], dfc_mul(A[j], kv));
     }
   }
   double kfact = 1.0;  // 1/k!
 #pragma unroll
   for (int k = 0; k < IP_KF; ++k) {
     if (k > 0) kfact /= (double)k;
-    spec[(int64_t)k * G + f] = make_double2(Cc[k].re * kfact, Cc[k].im * kfact);
+    spec[(int64_t)k * G + f] = dfc_scale(Cc[k], df_from_double(kfact));
   }
 }
 
@@ -321,7 +322,7 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 // term, base pixel.
 __global__ void __launch_bounds__(64)
 k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* __restrict__ start,
-              const double2* __restrict__ pos, const double* __restrict__ m, const double2* __restrict__ conv,
+              const double2* __restrict__ pos, const double* __restrict__ m, const float4* __restrict__ conv,
               MlpFar far, CellRec* __restrict__ recs, float2* __restrict__ coef, int64_t rc0, int64_t rc1) {
   const int64_t rc = rc0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (rc >= rc1) return;
@@ -382,13 +383,13 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
 #pragma unroll
     for (int k = 0; k < IP_KF; ++k) {
       if (k >= K) break;
-      const double2 v = conv[(int64_t)k * ncells + c];
+      const float4 v = conv[(int64_t)k * ncells + c];
       if (k < FIN_K64) {
-        acc[k].re += v.x;
-        acc[k].im += v.y;
+        acc[k].re += df_to_double(dfc_re(v));
+        acc[k].im += df_to_double(dfc_im(v));
       } else {
-        accf[k - FIN_K64].x += (float)v.x;
-        accf[k - FIN_K64].y += (float)v.y;
+        accf[k - FIN_K64].x += v.x + v.y;
+        accf[k - FIN_K64].y += v.z + v.w;
       }
     }
   }
@@ -1185,8 +1186,8 @@ irs_status interp_plan(irs_plan_t* P) {
   const size_t o_cnt = take(sizeof(int32_t) * ncells), o_start = take(sizeof(int32_t) * (ncells + 1));
   const size_t o_cur = take(sizeof(int32_t) * ncells);
   const size_t o_sb = take(sizeof(int32_t) * ((ncells + SCAN_B - 1) / SCAN_B + 1));
-  const size_t o_mp = take(sizeof(double2) * ig.P * ncells), o_conv = take(sizeof(double2) * IP_KF * ncells);
-  const size_t o_spec = take(sizeof(double2) * ig.P * G), o_kspec = take(sizeof(double2) * (ig.P + IP_KF - 1) * G);
+  const size_t o_mp = take(sizeof(float4) * ig.P * ncells), o_conv = take(sizeof(float4) * IP_KF * ncells);
+  const size_t o_spec = take(sizeof(float4) * ig.P * G), o_kspec = take(sizeof(float4) * (ig.P + IP_KF - 1) * G);
   const size_t o_rec = take(sizeof(CellRec) * nrc), o_coef = take(sizeof(float2) * ig.K * nrc);
   if (cudaMalloc(&S->ws, off) != cudaSuccess) {
     cudaGetLastError();
@@ -1199,10 +1200,10 @@ irs_status interp_plan(irs_plan_t* P) {
   S->cell_start = reinterpret_cast<int32_t*>(b + o_start);
   S->cell_cursor = reinterpret_cast<int32_t*>(b + o_cur);
   S->scan_blocks = reinterpret_cast<int32_t*>(b + o_sb);
-  S->mpole = reinterpret_cast<double2*>(b + o_mp);
-  S->conv = reinterpret_cast<double2*>(b + o_conv);
-  S->spec = reinterpret_cast<double2*>(b + o_spec);
-  S->kspec = reinterpret_cast<double2*>(b + o_kspec);
+  S->mpole = reinterpret_cast<float4*>(b + o_mp);
+  S->conv = reinterpret_cast<float4*>(b + o_conv);
+  S->spec = reinterpret_cast<float4*>(b + o_spec);
+  S->kspec = reinterpret_cast<float4*>(b + o_kspec);
   S->recs = reinterpret_cast<CellRec*>(b + o_rec);
   S->coef = reinterpret_cast<float2*>(b + o_coef);
   irs_status st = alloc_lens_buffers(S, nstar + nstar / 4 + 256);
