@@ -171,9 +171,7 @@ def ip_flops_fixed(variant):
 # dram__bytes_write.sum), valid only for the kernel build, workload and cell
 # size they were captured on: (workload, cell multiplier, variant) -> bytes.
 # Source: profiles/k_ip_ray_paper-mid-full.md.
-IP_TRAFFIC = {("paper-mid", 1.0, 7): 46.848768e6 + 11.264e3,
-              ("paper-mid", 0.71, 9): 75.718144e6 + 1.016576e6,
-              ("paper-mid", 0.85, 0): 58.065152e6 + 57.088e3}
+IP_TRAFFIC = {}
 
 
 def mean_near_lenses(info, xy):
@@ -777,6 +775,112 @@ def study_border(args):
     print(json.dumps(out))
 
 
+def batched_configs(n_maps=256, seed=4, max_rays=4.0e9):
+    """Seeded uneven maps: kappa_* in [0.1, 0.6], kappa_s / kappa in {0, 0.3,
+    0.6}, gamma in [0.1, 0.6], maps of 500^2 ... 2000^2 pixels over 10 ... 20
+    theta_E, 1e3 ... 1e5 lenses (log-uniform), 16 ... 100 rays per pixel.
+    Draws with |1 - kappa -+ gamma| < 0.15 (near-critical: the image plane
+    explodes) or more than max_rays rays are redrawn."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    while len(out) < n_maps:
+        ks = rng.uniform(0.1, 0.6)
+        frac = rng.choice([0.0, 0.3, 0.6])
+        kss = ks * frac / (1.0 - frac)
+        g = rng.uniform(0.1, 0.6)
+        kap = ks + kss
+        if min(abs(1 - kap - g), abs(1 - kap + g)) < 0.15:
+            continue
+        S = rng.uniform(10.0, 20.0)
+        npix = int(rng.integers(500, 2001))
+        nav = rng.uniform(16.0, 100.0)
+        n = int(round(10 ** rng.uniform(3.0, 5.0)))
+        P = 10.0 * np.sqrt(ks)
+        rays = nav * (npix / S) ** 2 * (S + 2 * P) ** 2 / abs((1 - kap - g) * (1 - kap + g))
+        if rays > max_rays:
+            continue
+        out.append(dict(kappa_star=ks, kappa_s=kss, gamma=g, S=S, npix=npix, nav=nav, n_star=n))
+    return out
+
+
+def study_batched(args):
+    """The batched persistent launch: 256 uneven maps through
+    irs_make_maps_batched (one captured CUDA graph, replayed), against one
+    irs_make_map per map on the same plans; per-map and total rays/s, and a
+    bitwise check that both give the same maps.  All plans use the setting
+    the autotuner picks at the paper-mid workload (cells 0.85 x the rule,
+    ray-pass variant 0), since one persistent launch serves one variant."""
+    torch, irs, lensgen = _study_env()
+    cfgs = batched_configs(args.batch_maps)
+    plans, lens, counts, rays = [], [], [], []
+    ws = 0
+    for k, c in enumerate(cfgs):
+        S = c["S"]
+        p = irs.make_params(c["kappa_star"], c["kappa_s"], c["gamma"], (-S / 2, S / 2, -S / 2, S / 2), c["npix"],
+                            c["nav"], n_star=c["n_star"], method=irs.IRS_INTERP, cell_mult=0.85, kernel_variant=0)
+        plan = irs.Plan(p)
+        inf = plan.info
+        ws += inf.workspace_bytes
+        if ws > 150e9:
+            raise RuntimeError("batched study workspace above 150 GB")
+        box = (inf.lens_x0, inf.lens_x1, inf.lens_y0, inf.lens_y1)
+        area = (box[1] - box[0]) * (box[3] - box[2])
+        xy, m = lensgen.lens_field(c["n_star"], box, shape="uniform", seed=1000 + k,
+                                   total_mass=c["kappa_star"] * area / np.pi)
+        plans.append(plan)
+        lens.append((torch.from_numpy(xy).cuda(), torch.from_numpy(m).cuda()))
+        counts.append(torch.zeros((c["npix"], c["npix"]), dtype=torch.uint32, device="cuda"))
+        rays.append(int(inf.n_rays))
+    total = float(sum(rays))
+    stream = torch.cuda.current_stream()
+    # one map per call
+    per = []
+    for plan, (xy, m), cnt in zip(plans, lens, counts):
+        irs.irs_make_map(plan.handle, xy, m, cnt)  # warm-up (allocations, first launch)
+    torch.cuda.synchronize()
+    singles = []
+    t_seq = 0.0
+    for plan, (xy, m), cnt, r in zip(plans, lens, counts, rays):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        irs.irs_make_map(plan.handle, xy, m, cnt)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        t_seq += ms
+        per.append(r / (ms * 1e-3))
+        singles.append(cnt.clone())
+    # the batch: capture on the first call, then replays
+    hs = [p.handle for p in plans]
+    xs, ms_ = [x for x, _ in lens], [m for _, m in lens]
+    for _ in range(max(args.warmup, 1)):
+        irs.irs_make_maps_batched(hs, xs, ms_, counts)
+    torch.cuda.synchronize()
+    steps = max(args.steps, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        irs.irs_make_maps_batched(hs, xs, ms_, counts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / steps
+    same = sum(int(torch.equal(a, b)) for a, b in zip(singles, counts))
+    per = np.array(per)
+    out = {"study": "batched", "maps": len(cfgs), "total_rays": total,
+           "config": "kappa_* 0.1-0.6, kappa_s/kappa {0,0.3,0.6}, gamma 0.1-0.6, 500^2-2000^2 px over "
+                     "10-20 theta_E, 1e3-1e5 uniform-mass lenses, 16-100 rays/px (seeded)",
+           "setting": {"cell_mult": 0.85, "kernel_variant": 0},
+           "batched": {"ms": t_batch, "rays_per_s": total / (t_batch * 1e-3), "steps": steps},
+           "sequential": {"ms": t_seq, "rays_per_s": total / (t_seq * 1e-3)},
+           "per_map_rays_per_s": {"min": float(per.min()), "median": float(np.median(per)),
+                                  "max": float(per.max())},
+           "rays_per_map": {"min": min(rays), "median": float(np.median(rays)), "max": max(rays)},
+           "maps_identical_to_single_calls": same, "workspace_gb": ws / 1e9}
+    for p in plans:
+        p.close()
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     world, rank, local = dist_init()
@@ -837,16 +941,18 @@ def main():
     ap.add_argument("--n-star", type=int, default=0, help="override the lens count (profiling)")
     ap.add_argument("--npix", type=int, default=0, help="override the map side (profiling)")
     ap.add_argument("--nav", type=float, default=0.0, help="override rays per pixel (profiling)")
-    ap.add_argument("--study", default="", choices=["", "accuracy", "planes", "border"],
+    ap.add_argument("--study", default="", choices=["", "accuracy", "planes", "border", "batched"],
                     help="one of the paper's side measurements instead of the benchmark (one GPU)")
     ap.add_argument("--ref-rays", type=float, default=4.0e10, help="rays of the accuracy study's reference map")
+    ap.add_argument("--batch-maps", type=int, default=256, help="maps of the batched study")
     ap.add_argument("--shard", default="replicas", choices=["replicas", "strips"],
                     help="N > 1: a map per rank (weak scaling) or one map in row strips (strong)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.study:
-        {"accuracy": study_accuracy, "planes": study_planes, "border": study_border}[args.study](args)
+        {"accuracy": study_accuracy, "planes": study_planes, "border": study_border,
+         "batched": study_batched}[args.study](args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -602,8 +602,13 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   __shared__ int blk_start[9], blk_off[10];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t k = ig.k;
+  // Every FP32 step of the cell's ray geometry below is written with explicit
+  // rounding (__fadd_rn, __fmul_rn, __fdiv_rn, fmaf): implicit contraction
+  // would depend on how the compiler places the code in each kernel that
+  // inlines this function, and the single-map and batched ray passes must
+  // give the same maps bit for bit.
   const float hf = (float)ig.h;
-  const float inv_k = 1.0f / (float)k;
+  const float inv_k = __fdiv_rn(1.0f, (float)k);
 
   const int rcx = (int)(rc % ig.nrcx), rcy = (int)(rc / ig.nrcx);
   const int cx = rcx + ig.ox, cy = rcy + ig.oy;
@@ -644,16 +649,16 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     int q = 0;
     while (q < 8 && t >= blk_off[q + 1]) ++q;
     const float4 v = a.rel[blk_start[q] + (t - blk_off[q])];
-    const float ox = (float)((q % 3) - 1) * hf, oy = (float)((q / 3) - 1) * hf;
-    const float x = v.x + ox, y = v.y + oy;
+    const float ox = __fmul_rn((float)((q % 3) - 1), hf), oy = __fmul_rn((float)((q / 3) - 1), hf);
+    const float x = __fadd_rn(v.x, ox), y = __fadd_rn(v.y, oy);
     nxy_s[t] = make_float4(-x, -x, -y, -y);
     nm_s[t] = make_float2(-v.z, -v.z);
   }
   // level 2: re-centre the series on the sub-cell centres eps (cell units)
   for (int t = tid; t < Q * Q * K2; t += blockDim.x) {
     const int sub = t / K2, nn = t % K2;
-    const float er = ((float)(sub % Q) + 0.5f) / Q - 0.5f;
-    const float ei = ((float)(sub / Q) + 0.5f) / Q - 0.5f;
+    const float er = __fsub_rn(__fdiv_rn(__fadd_rn((float)(sub % Q), 0.5f), (float)Q), 0.5f);
+    const float ei = __fsub_rn(__fdiv_rn(__fadd_rn((float)(sub / Q), 0.5f), (float)Q), 0.5f);
     float sr = 0.f, si = 0.f, tr = 1.f, ti = 0.f;  // term = binom(kk, nn) eps^(kk - nn)
     for (int kk = nn; kk < ig.K; ++kk) {
       if (kk >= 1) {
@@ -661,13 +666,15 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
         sr = fmaf(c.x, tr, fmaf(-c.y, ti, sr));
         si = fmaf(c.x, ti, fmaf(c.y, tr, si));
       }
-      const float f = (float)(kk + 1) / (float)(kk + 1 - nn);
-      const float nr = (tr * er - ti * ei) * f, ni = (tr * ei + ti * er) * f;
+      const float f = __fdiv_rn((float)(kk + 1), (float)(kk + 1 - nn));
+      const float nr = __fmul_rn(fmaf(tr, er, -__fmul_rn(ti, ei)), f);
+      const float ni = __fmul_rn(fmaf(tr, ei, __fmul_rn(ti, er)), f);
       tr = nr;
       ti = ni;
     }
-    const float sc = powf((float)Q, -(float)nn);
-    const float cr = sr * sc, ci = -(si * sc);
+    float sc = 1.0f;  // Q^-nn
+    for (int i = 0; i < nn; ++i) sc = __fdiv_rn(sc, (float)Q);
+    const float cr = __fmul_rn(sr, sc), ci = -__fmul_rn(si, sc);
     sub_s[t] = make_float4(cr, cr, ci, ci);
   }
   // row table: t_y = tau_y h, sigma_y = (l + 1/2) Q / k - v - 1/2, v Q, rows of
@@ -680,10 +687,10 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int l = 2 * pr + j;
-      const float sv = ((float)l + 0.5f) * ((float)Q * inv_k);
+      const float sv = __fmul_rn(__fadd_rn((float)l, 0.5f), __fmul_rn((float)Q, inv_k));
       const int v = min(__float2int_rd(sv), Q - 1);
-      tyv[j] = fmaf((float)l, inv_k, 0.5f * inv_k - 0.5f) * hf;
-      sg[j] = sv - (float)v - 0.5f;
+      tyv[j] = __fmul_rn(fmaf((float)l, inv_k, fmaf(0.5f, inv_k, -0.5f)), hf);
+      sg[j] = __fsub_rn(__fsub_rn(sv, (float)v), 0.5f);
       vq[j] = v * Q;
     }
     rp.ty = make_float2(tyv[0], tyv[1]);
@@ -704,8 +711,8 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   const int kx = (int)(i1 - i0), ylo = (int)(jlo - j0), yhi = (int)(jhi - j0);
   const int ylo2 = ylo & ~1;
   const int npair = (yhi + 1) >> 1;
-  const float c_tau = 0.5f * inv_k - 0.5f;  // tau = (l + 1/2)/k - 1/2
-  const float qk = (float)Q * inv_k;        // sub-cell index = floor((l + 1/2) Q / k)
+  const float c_tau = fmaf(0.5f, inv_k, -0.5f);  // tau = (l + 1/2)/k - 1/2
+  const float qk = __fmul_rn((float)Q, inv_k);   // sub-cell index = floor((l + 1/2) Q / k)
   const float fnan = __int_as_float(0x7fffffff);
   // work units (32-column strip x R-row group), dealt round-robin to warps
   const int nwarps = blockDim.x / 32;
@@ -717,13 +724,13 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     const int cl = st * 32 + lane;
     const int rl0 = ylo2 + rg * R;
     const int p0 = rl0 >> 1;
-    const float su = ((float)cl + 0.5f) * qk;
+    const float su = __fmul_rn(__fadd_rn((float)cl, 0.5f), qk);
     const int u = min(__float2int_rd(su), Q - 1);
-    const float sgr = su - (float)u - 0.5f;
+    const float sgr = __fsub_rn(__fsub_rn(su, (float)u), 0.5f);
     // rays outside the cell's columns get a NaN x, rays outside its rows a NaN
     // y accumulator: both reach beta whatever the near sum does and fail the
     // pixel test
-    const float tx = cl < kx ? fmaf((float)cl, inv_k, c_tau) * hf : fnan;
+    const float tx = cl < kx ? __fmul_rn(fmaf((float)cl, inv_k, c_tau), hf) : fnan;
     const float2 TX = make_float2(tx, tx), SGR = make_float2(sgr, sgr);
     float2 TY[R / 2], NAX[R / 2], NAY[R / 2];
 #pragma unroll
@@ -827,11 +834,11 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
             for (int c = 0; c < n_corner; ++c) {
-              const float wr = rec_s.corner[c][0] + tx, wi = rec_s.corner[c][1] + tyr[j];
-              const float lr = 0.5f * logf(wr * wr + wi * wi), li = atan2f(wi, wr);
-              const float plr = wr * lr - wi * li, pli = wr * li + wi * lr;
-              qr[j] += rec_s.corner[c][2] * pli;
-              qi[j] += rec_s.corner[c][2] * plr;
+              const float wr = __fadd_rn(rec_s.corner[c][0], tx), wi = __fadd_rn(rec_s.corner[c][1], tyr[j]);
+              const float lr = __fmul_rn(0.5f, logf(fmaf(wr, wr, __fmul_rn(wi, wi)))), li = atan2f(wi, wr);
+              const float plr = fmaf(wr, lr, -__fmul_rn(wi, li)), pli = fmaf(wr, li, __fmul_rn(wi, lr));
+              qr[j] = fmaf(rec_s.corner[c][2], pli, qr[j]);
+              qi[j] = fmaf(rec_s.corner[c][2], plr, qi[j]);
             }
           }
           QR[i] = make_float2(qr[0], qr[1]);
