@@ -391,6 +391,8 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
                                                       32 * (BR_TY / R), 0) != cudaSuccess)      \
       per_sm = 1;                                                                               \
     break;
+int brute_num_variants() { return BR_NVARIANT; }
+
 int brute_grid_size(int num_sms, int variant) {
   int per_sm = 0;
   switch (variant) { BR_VARIANTS(BR_DECL_OCC) default: break; }

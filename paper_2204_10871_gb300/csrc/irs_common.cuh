@@ -199,6 +199,7 @@ cudaError_t launch_brute_dump(const irs_plan_t* P, const double* xy, const doubl
                               cudaStream_t s);
 cudaError_t launch_magnify(const irs_plan_t* P, const uint32_t* counts, float* mag, cudaStream_t s);
 int brute_grid_size(int num_sms, int variant);
+int brute_num_variants();
 // FP64 sizing of the plane and lattice (irs_api.cu)
 irs_status size_plane(irs_plan_t* P);
 }  // namespace irs
