@@ -555,6 +555,16 @@ struct IpRayArgs {
   X(9, 8, 8, 8, 3, 0, 0)
 constexpr int IP_NVARIANT = 10;
 
+// Advance a (strip, row group) position by `by` units of a row-major
+// nstrip-wide unit grid.
+__device__ __forceinline__ void step_unit(int& st, int& rg, int by, int nstrip) {
+  st += by;
+  while (st >= nstrip) {
+    st -= nstrip;
+    ++rg;
+  }
+}
+
 // Row data of one pair of cell rows (2l, 2l + 1), read by the ray pass.
 struct __align__(16) IpRowPair {
   float2 sgi;   // sigma_y = (l + 1/2) Q / k - v - 1/2 of both rows
@@ -719,8 +729,10 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   const int nstrip = (kx + 31) / 32;
   const int nrg = (yhi - ylo2 + R - 1) / R;
   const int nunit = nstrip * nrg;
-  for (int unit = warp; unit < nunit; unit += nwarps) {
-    const int st = unit % nstrip, rg = unit / nstrip;
+  // (strip, row group) of the warp's first unit, then stepped by nwarps units
+  // at a time: no integer division per unit
+  int st = warp % nstrip, rg = warp / nstrip;
+  for (int unit = warp; unit < nunit; unit += nwarps, step_unit(st, rg, nwarps, nstrip)) {
     const int cl = st * 32 + lane;
     const int rl0 = ylo2 + rg * R;
     const int p0 = rl0 >> 1;
