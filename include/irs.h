@@ -190,8 +190,10 @@ irs_status irs_shoot_rays(irs_plan_t* plan, const double* lens_xy, const double*
 
 /* Autotuner (no paper counterpart; the paper fixes Delta x1 by its rule and
  * Delta x2 = Delta x1 / 20 "after a series of tests", Sec. 2.4): for an
- * INTERP or MLP `params`, time candidate level-1 cell sizes (multipliers 0.5 ..
- * 2 of the paper's rule) and ray-pass kernel variants on the given lenses
+ * INTERP or MLP `params`, time candidate level-1 cell sizes (multiples of 32
+ * rays from 0.5 to 1.25 times the paper's rule, and the rule itself; for rule
+ * cells under 128 rays, multipliers 0.5 .. 2 of the rule) and ray-pass kernel
+ * variants on the given lenses
  * (device arrays as irs_make_map) and write into *tuned a copy of *params with
  * the fastest cell_mult and kernel_variant.  Each candidate's cost per map is
  * its measured cell-list and far-field time plus its ray-pass time on a band

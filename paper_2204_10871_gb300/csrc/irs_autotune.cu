@@ -1,10 +1,14 @@
 // irs_autotune.cu -- choose the level-1 cell size and the ray-pass kernel
 // variant of the interpolated method by timing them on the caller's lenses.
 //
-// Candidates: cell multiplier (of the paper's Delta x1 rule) in {0.5, 0.71,
-// 1, 1.41, 2} times the ray-pass variants (rays per thread, level-2 sub-cells,
-// sub-cell terms, CTAs per SM, binning), skipping cells wider than both
-// 2 theta_E and the paper rule's cell (FP32 near-field precision).  Each candidate plan makes one warm-up and one
+// Candidates: level-1 cell sizes times the ray-pass variants (rays per
+// thread, level-2 sub-cells, sub-cell terms, CTAs per SM, binning, shared
+// reciprocals), skipping cells wider than both 2 theta_E and the paper rule's
+// cell (FP32 near-field precision).  The ray pass deals 32-column strips of a
+// cell to warps, so where the rule's cell is at least 128 rays wide the sizes
+// are the multiples of 32 rays from 0.5 to 1.25 rule cells (no idle lanes in
+// a cell's last strip) and the rule itself; narrower rule cells take the
+// multipliers 0.5 ... 2 of the rule.  Each candidate plan makes one warm-up and one
 // timed map restricted to a band of lattice rows holding about 2e9 rays (the
 // whole lattice when smaller); its cost per map is the measured cell-list and
 // far-field time plus the ray-pass time scaled to the full lattice.  Results
@@ -15,8 +19,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <iterator>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "irs_common.cuh"
 
@@ -24,6 +30,22 @@ namespace {
 
 const double CELL_MULTS[] = {0.5, 0.6, 0.70710678, 0.85, 1.0, 1.2, 1.41421356, 2.0};
 constexpr int NVARIANT = 10;
+constexpr int STRIP_RAYS = 32;  // columns of a ray-pass work unit (one per lane)
+
+// Cell multipliers to try for a rule cell of `rule_rays` ray spacings.  The
+// plan takes k = ceil(mult * rule_rays) rays per side, so (k - 1/2) / rule_rays
+// gives exactly k.
+std::vector<double> cell_candidates(double rule_rays) {
+  std::vector<double> m;
+  if (rule_rays >= 4.0 * STRIP_RAYS) {
+    for (int k = 2 * STRIP_RAYS; k <= 1024; k += STRIP_RAYS)
+      if (k >= 0.5 * rule_rays && k <= 1.25 * rule_rays) m.push_back(((double)k - 0.5) / rule_rays);
+    m.push_back(1.0);
+  } else {
+    m.assign(std::begin(CELL_MULTS), std::end(CELL_MULTS));
+  }
+  return m;
+}
 constexpr double BAND_RAYS = 2.0e9;
 std::mutex g_file_mu;
 
@@ -155,7 +177,7 @@ extern "C" irs_status irs_autotune(const irs_params* params, const double* lens_
     return IRS_ERR_OOM;
   }
   // the paper rule's cell side, the reference for the size guard
-  double h_rule = 0.0;
+  double h_rule = 0.0, rule_rays = 0.0;
   {
     irs_params p = *params;
     p.method = IRS_INTERP;
@@ -166,11 +188,12 @@ extern "C" irs_status irs_autotune(const irs_params* params, const double* lens_
       irs_plan_info info;
       irs_plan_info_get(P, &info);
       h_rule = info.cell_x;
+      rule_rays = irs::interp_rule_rays(P);
       irs_plan_destroy(P);
     }
   }
   double best = -1.0;
-  for (double m : CELL_MULTS) {
+  for (double m : cell_candidates(rule_rays)) {
     for (int v = 0; v < NVARIANT; ++v) {
       const double t = measure(*params, m, v, lens_xy, mass, n, counts, h_rule, s);
       if (t < 0) continue;

@@ -202,6 +202,9 @@ int brute_grid_size(int num_sms, int variant);
 int brute_num_variants();
 // FP64 sizing of the plane and lattice (irs_api.cu)
 irs_status size_plane(irs_plan_t* P);
+// the flow chart's level-1 cell side in ray spacings, before the cell
+// multiplier (irs_interp.cu; 0 for plans without interpolation state)
+double interp_rule_rays(const irs_plan_t* P);
 }  // namespace irs
 
 // cached batch graphs that use a plan are dropped with it (irs_batch.cu)

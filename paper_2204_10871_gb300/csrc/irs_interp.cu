@@ -73,6 +73,7 @@ struct IpGeo {
 
 struct InterpState {
   IpGeo ig;
+  double rule_rays;  // the flow chart's Delta x1 in ray spacings, before the multiplier
   Fft2d fft;
   void* ws;
   size_t ws_bytes;
@@ -573,10 +574,14 @@ struct __align__(16) IpRowPair {
   int32_t v0, v1;  // level-2 row offset v Q of both rows
 };
 
+// Row stride (float2) of the per-cell table of scaled series coefficients:
+// odd, so that the K2 rows a warp reads at once fall in distinct banks.
+constexpr int IP_CB_STRIDE = IP_KMAX + 1;
+
 // Dynamic shared memory of the ray pass (bytes, 16-byte aligned blocks):
 // near lenses as (-x, -x, -y, -y) and (-m, -m) pairs, the level-2 series
 // as conj duplicated (c.re, c.re, -c.im, -c.im), the row table and the
-// level-1 series.
+// level-1 series scaled for the re-centring, one row per level-2 term.
 template <int Q, int K2>
 struct IpSmem {
   static constexpr size_t near_xy = 0;
@@ -584,7 +589,7 @@ struct IpSmem {
   static constexpr size_t sub = near_m + sizeof(float2) * IP_NEAR_MAX;
   static constexpr size_t rows = sub + sizeof(float4) * Q * Q * K2;
   static constexpr size_t coef = rows + sizeof(IpRowPair) * (IP_KMAX_RAYS / 2);
-  static constexpr size_t bytes = coef + sizeof(float2) * IP_KMAX;
+  static constexpr size_t bytes = (coef + sizeof(float2) * K2 * IP_CB_STRIDE + 15) / 16 * 16;
 };
 
 // One level-1 cell: gather the 3x3 block's lenses, re-centre the series on the
@@ -607,7 +612,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   float2* nm_s = reinterpret_cast<float2*>(ip_smem + L::near_m);
   float4* sub_s = reinterpret_cast<float4*>(ip_smem + L::sub);
   IpRowPair* row_s = reinterpret_cast<IpRowPair*>(ip_smem + L::rows);
-  float2* c_s = reinterpret_cast<float2*>(ip_smem + L::coef);
+  float2* cb_s = reinterpret_cast<float2*>(ip_smem + L::coef);
   __shared__ CellRec rec_s;
   __shared__ int blk_start[9], blk_off[10];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -652,7 +657,25 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     }
     blk_off[9] = off;
   }
-  for (int q = tid; q < ig.K; q += blockDim.x) c_s[q] = a.coef[rc * ig.K + q];
+  // Level 2 re-centres the cell series sum_kk c_kk w^kk (w in cell units,
+  // terms from 1: term 0 sits in the cell's base) on the sub-cell centres
+  // eps: with w = eps + sigma / Q the coefficient of sigma^n is
+  // Q^-n sum_kk binom(kk, n) c_kk eps^(kk - n).  First the per-cell table
+  // cb[n][kk] = Q^-n binom(kk, n) c_kk (binomials exact in FP32 for kk < 32).
+  const float inv_q = __fdiv_rn(1.0f, (float)Q);
+  for (int t = tid; t < K2 * ig.K; t += blockDim.x) {
+    const int nn = t / ig.K, kk = t % ig.K;
+    float2 v = make_float2(0.f, 0.f);
+    if (kk >= nn && kk >= 1) {
+      int b = 1;  // binom(kk, nn), exact integer steps
+      for (int i = 1; i <= nn; ++i) b = b * (kk - nn + i) / i;
+      float sc = (float)b;
+      for (int i = 0; i < nn; ++i) sc = __fmul_rn(sc, inv_q);
+      const float2 c = a.coef[rc * ig.K + kk];
+      v = make_float2(__fmul_rn(c.x, sc), __fmul_rn(c.y, sc));
+    }
+    cb_s[nn * IP_CB_STRIDE + kk] = v;
+  }
   __syncthreads();
   const int n_near = blk_off[9];
   for (int t = tid; t < n_near; t += blockDim.x) {
@@ -664,28 +687,21 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     nxy_s[t] = make_float4(-x, -x, -y, -y);
     nm_s[t] = make_float2(-v.z, -v.z);
   }
-  // level 2: re-centre the series on the sub-cell centres eps (cell units)
+  // then per (sub-cell, n) the polynomial sum_j cb[n][n + j] eps^j by Horner
   for (int t = tid; t < Q * Q * K2; t += blockDim.x) {
     const int sub = t / K2, nn = t % K2;
-    const float er = __fsub_rn(__fdiv_rn(__fadd_rn((float)(sub % Q), 0.5f), (float)Q), 0.5f);
-    const float ei = __fsub_rn(__fdiv_rn(__fadd_rn((float)(sub / Q), 0.5f), (float)Q), 0.5f);
-    float sr = 0.f, si = 0.f, tr = 1.f, ti = 0.f;  // term = binom(kk, nn) eps^(kk - nn)
-    for (int kk = nn; kk < ig.K; ++kk) {
-      if (kk >= 1) {
-        const float2 c = c_s[kk];
-        sr = fmaf(c.x, tr, fmaf(-c.y, ti, sr));
-        si = fmaf(c.x, ti, fmaf(c.y, tr, si));
-      }
-      const float f = __fdiv_rn((float)(kk + 1), (float)(kk + 1 - nn));
-      const float nr = __fmul_rn(fmaf(tr, er, -__fmul_rn(ti, ei)), f);
-      const float ni = __fmul_rn(fmaf(tr, ei, __fmul_rn(ti, er)), f);
-      tr = nr;
-      ti = ni;
+    const float er = __fmaf_rn(__fadd_rn((float)(sub % Q), 0.5f), inv_q, -0.5f);
+    const float ei = __fmaf_rn(__fadd_rn((float)(sub / Q), 0.5f), inv_q, -0.5f);
+    const float2* cb = cb_s + nn * IP_CB_STRIDE;
+    float sr = 0.f, si = 0.f;
+#pragma unroll 2
+    for (int kk = ig.K - 1; kk >= nn; --kk) {
+      const float2 c = cb[kk];
+      const float nr = __fmaf_rn(sr, er, __fmaf_rn(-si, ei, c.x));
+      si = __fmaf_rn(sr, ei, __fmaf_rn(si, er, c.y));
+      sr = nr;
     }
-    float sc = 1.0f;  // Q^-nn
-    for (int i = 0; i < nn; ++i) sc = __fdiv_rn(sc, (float)Q);
-    const float cr = __fmul_rn(sr, sc), ci = -__fmul_rn(si, sc);
-    sub_s[t] = make_float4(cr, cr, ci, ci);
+    sub_s[t] = make_float4(sr, sr, -si, -si);
   }
   // row table: t_y = tau_y h, sigma_y = (l + 1/2) Q / k - v - 1/2, v Q, rows of
   // the whole cell side in pairs (a last odd row's partner is never binned)
@@ -1148,7 +1164,9 @@ irs_status interp_plan(irs_plan_t* P) {
   if (nstar < 1) nstar = 1;
   // level-1 resolution, flow chart: Delta x1 = min(L0, min(I_x, I_y)/10)
   const double L0 = sqrt(Ix * Iy / (double)nstar);
-  double dx1 = fmin(L0, fmin(Ix, Iy) / 10.0) * (p.cell_mult > 0 ? p.cell_mult : 1.0);
+  const double dx1_rule = fmin(L0, fmin(Ix, Iy) / 10.0);
+  S->rule_rays = dx1_rule / g.dx3;
+  double dx1 = dx1_rule * (p.cell_mult > 0 ? p.cell_mult : 1.0);
   int64_t k = (int64_t)ceil(dx1 / g.dx3 - 1e-9);
   if (k < 4) k = 4;
   if (k > IP_KMAX_RAYS) k = IP_KMAX_RAYS;  // the ray pass keeps a row table per cell
@@ -1244,6 +1262,7 @@ irs_status interp_plan(irs_plan_t* P) {
 }
 
 double interp_cell_side(const irs_plan_t* P) { return S_(P) ? S_(P)->ig.h : 0.0; }
+double interp_rule_rays(const irs_plan_t* P) { return S_(P) ? S_(P)->rule_rays : 0.0; }
 
 void interp_fill_info(const irs_plan_t* P, irs_plan_info* info) {
   const InterpState* S = S_(P);
