@@ -60,6 +60,8 @@ struct __align__(16) CellRec {
   float corner[IP_MAX_CORNER][4];    // (z_C - c).re, .im, a_c, 0: corners evaluated per ray
 };
 
+static_assert(sizeof(CellRec) % 4 == 0 && sizeof(CellRec) / 4 <= 32, "a warp copies a cell record word by word");
+
 struct IpGeo {
   int64_t k;           // rays per cell side
   double h;            // cell side
@@ -69,6 +71,8 @@ struct IpGeo {
   double gx0, gy0;     // grid origin (lower-left corner of cell (0,0))
   int K, P, W;
   int variant;  // ray-pass kernel variant (R, Q, K2)
+  float hf;     // (float) h
+  float inv_k;  // 1 / k in FP32 (correctly rounded)
 };
 
 struct InterpState {
@@ -622,8 +626,8 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   // would depend on how the compiler places the code in each kernel that
   // inlines this function, and the single-map and batched ray passes must
   // give the same maps bit for bit.
-  const float hf = (float)ig.h;
-  const float inv_k = __fdiv_rn(1.0f, (float)k);
+  const float hf = ig.hf;
+  const float inv_k = ig.inv_k;
 
   const int rcx = (int)(rc % ig.nrcx), rcy = (int)(rc / ig.nrcx);
   const int cx = rcx + ig.ox, cy = rcy + ig.oy;
@@ -636,26 +640,38 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     if (jlo >= jhi) return;  // uniform over the CTA
   }
   __syncthreads();  // previous cell's shared data no longer read
-  if (tid == 0) {
-    rec_s = a.recs[rc];
-    int off = 0;
-    for (int q = 0; q < 9; ++q) {
-      const int x = cx + (q % 3) - 1, y = cy + (q / 3) - 1;
-      int s0 = 0, cnt = 0;
+  if (warp == 0) {
+    // lane q < 9 takes cell q of the 3x3 block (row-major from the lower
+    // left); the block's lens offsets are the exclusive prefix sum of the counts
+    int s0 = 0, cnt = 0;
+    if (lane < 9) {
+      const int x = cx + (lane % 3) - 1, y = cy + (lane / 3) - 1;
       if (x >= 0 && x < ig.ncx && y >= 0 && y < ig.ncy) {
         const int64_t s = (int64_t)y * ig.ncx + x;
         s0 = a.start[s];
         cnt = a.start[s + 1] - s0;
       }
-      blk_start[q] = s0;
-      blk_off[q] = off;
-      off += cnt;
     }
-    if (off > IP_NEAR_MAX) {
-      atomicExch(a.status, (int)IRS_ERR_OVERFLOW);
-      off = IP_NEAR_MAX;
+    int inc = cnt;
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+      const int v = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+      if (lane >= d) inc += v;
     }
-    blk_off[9] = off;
+    if (lane < 9) {
+      blk_start[lane] = s0;
+      blk_off[lane] = inc - cnt;
+    }
+    if (lane == 8) {
+      int off = inc;
+      if (off > IP_NEAR_MAX) {
+        atomicExch(a.status, (int)IRS_ERR_OVERFLOW);
+        off = IP_NEAR_MAX;
+      }
+      blk_off[9] = off;
+    }
+  } else if (warp == 1 && lane < (int)(sizeof(CellRec) / 4)) {
+    reinterpret_cast<uint32_t*>(&rec_s)[lane] = reinterpret_cast<const uint32_t*>(a.recs + rc)[lane];
   }
   // Level 2 re-centres the cell series sum_kk c_kk w^kk (w in cell units,
   // terms from 1: term 0 sits in the cell's base) on the sub-cell centres
@@ -1172,6 +1188,8 @@ irs_status interp_plan(irs_plan_t* P) {
   if (k > IP_KMAX_RAYS) k = IP_KMAX_RAYS;  // the ray pass keeps a row table per cell
   ig.k = k;
   ig.h = (double)k * g.dx3;
+  ig.hf = (float)ig.h;
+  ig.inv_k = 1.0f / (float)k;
   ig.nrcx = (int32_t)((g.nrx + k - 1) / k);
   ig.nrcy = (int32_t)((g.nry + k - 1) / k);
   // lens region: the rectangle, or the circumscribed circle's bounding box
