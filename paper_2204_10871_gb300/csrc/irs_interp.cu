@@ -578,6 +578,10 @@ struct __align__(16) IpRowPair {
   int32_t v0, v1;  // level-2 row offset v Q of both rows
 };
 
+// Row pairs of the row table past the cell's last: a thread's R / 2 pairs
+// are read without clamping the index (R <= 2 IP_ROW_PAD).
+constexpr int IP_ROW_PAD = 4;
+
 // Row stride (float2) of the per-cell table of scaled series coefficients:
 // odd, so that the K2 rows a warp reads at once fall in distinct banks.
 constexpr int IP_CB_STRIDE = IP_KMAX + 1;
@@ -592,7 +596,7 @@ struct IpSmem {
   static constexpr size_t near_m = near_xy + sizeof(float4) * IP_NEAR_MAX;
   static constexpr size_t sub = near_m + sizeof(float2) * IP_NEAR_MAX;
   static constexpr size_t rows = sub + sizeof(float4) * Q * Q * K2;
-  static constexpr size_t coef = rows + sizeof(IpRowPair) * (IP_KMAX_RAYS / 2);
+  static constexpr size_t coef = rows + sizeof(IpRowPair) * (IP_KMAX_RAYS / 2 + IP_ROW_PAD);
   static constexpr size_t bytes = (coef + sizeof(float2) * K2 * IP_CB_STRIDE + 15) / 16 * 16;
 };
 
@@ -720,8 +724,10 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     sub_s[t] = make_float4(sr, sr, -si, -si);
   }
   // row table: t_y = tau_y h, sigma_y = (l + 1/2) Q / k - v - 1/2, v Q, rows of
-  // the whole cell side in pairs (a last odd row's partner is never binned)
-  const int npair_cell = (int)((k + 1) >> 1);
+  // the whole cell side in pairs and R / 2 pairs past it (rows past the cell
+  // side are never binned; their sub-cell row is clamped to Q - 1)
+  static_assert(R <= 2 * IP_ROW_PAD, "row table padding");
+  const int npair_cell = (int)((k + 1) >> 1) + R / 2;
   for (int pr = tid; pr < npair_cell; pr += blockDim.x) {
     IpRowPair rp;
     float tyv[2], sg[2];
@@ -752,7 +758,6 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   // start on an even row so that row pairs line up with the table
   const int kx = (int)(i1 - i0), ylo = (int)(jlo - j0), yhi = (int)(jhi - j0);
   const int ylo2 = ylo & ~1;
-  const int npair = (yhi + 1) >> 1;
   const float c_tau = fmaf(0.5f, inv_k, -0.5f);  // tau = (l + 1/2)/k - 1/2
   const float qk = __fmul_rn((float)Q, inv_k);   // sub-cell index = floor((l + 1/2) Q / k)
   const float fnan = __int_as_float(0x7fffffff);
@@ -779,10 +784,16 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     float2 TY[R / 2], NAX[R / 2], NAY[R / 2];
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
-      TY[i] = row_s[min(p0 + i, npair - 1)].ty;
-      const int ra = rl0 + 2 * i;
+      TY[i] = row_s[p0 + i].ty;
       NAX[i] = make_float2(0.f, 0.f);
-      NAY[i] = make_float2(ra >= ylo && ra < yhi ? 0.f : fnan, ra + 1 < yhi ? 0.f : fnan);
+      NAY[i] = make_float2(0.f, 0.f);
+    }
+    if (rl0 < ylo || rl0 + R > yhi) {  // a group at the band's edge (uniform over the warp)
+#pragma unroll
+      for (int i = 0; i < R / 2; ++i) {
+        const int ra = rl0 + 2 * i;
+        NAY[i] = make_float2(ra >= ylo && ra < yhi ? 0.f : fnan, ra + 1 < yhi ? 0.f : fnan);
+      }
     }
 #pragma unroll 2
     for (int q = 0; q < n_near; ++q) {
@@ -818,7 +829,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
         bool aligned = true;  // no pair straddles a sub-cell row: uniform over the warp
 #pragma unroll
         for (int i = 0; i < HP; ++i) {
-          const IpRowPair* rp = row_s + min(p0 + h + i, npair - 1);
+          const IpRowPair* rp = row_s + p0 + h + i;
           SG[i] = *reinterpret_cast<const float4*>(rp);
           const int2 v = *reinterpret_cast<const int2*>(&rp->v0);
           va[i] = (v.x + u) * K2;
@@ -847,7 +858,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
         } else {
           int vb[HP];
 #pragma unroll
-          for (int i = 0; i < HP; ++i) vb[i] = (row_s[min(p0 + h + i, npair - 1)].v1 + u) * K2;
+          for (int i = 0; i < HP; ++i) vb[i] = (row_s[p0 + h + i].v1 + u) * K2;
 #pragma unroll
           for (int i = 0; i < HP; ++i) {
             const float4 ea = sub_s[va[i] + K2 - 1], eb = sub_s[vb[i] + K2 - 1];
@@ -873,7 +884,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
 #pragma unroll
         for (int i = 0; i < HP; ++i) {
           float qr[2] = {QR[i].x, QR[i].y}, qi[2] = {QI[i].x, QI[i].y};
-          const float2 ty = row_s[min(p0 + h + i, npair - 1)].ty;
+          const float2 ty = row_s[p0 + h + i].ty;
           const float tyr[2] = {ty.x, ty.y};
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
@@ -895,7 +906,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
       uint32_t key[2 * HP];
 #pragma unroll
       for (int i = 0; i < HP; ++i) {
-        const float2 ty = row_s[min(p0 + h + i, npair - 1)].ty;
+        const float2 ty = row_s[p0 + h + i].ty;
         const float4 cx4 = make_float4(rec_s.bx_hi, rec_s.bx_hi, rec_s.bx_lo, rec_s.bx_lo);
         const float4 cy4 = make_float4(rec_s.by_hi, rec_s.by_hi, rec_s.by_lo, rec_s.by_lo);
         const float4 lm4 = make_float4(g.lam_s1, g.lam_s1, g.lam_s2, g.lam_s2);
