@@ -570,12 +570,11 @@ __device__ __forceinline__ void step_unit(int& st, int& rg, int by, int nstrip) 
   }
 }
 
-// Row data of one pair of cell rows (2l, 2l + 1), read by the ray pass.
+// Row table of a cell, one entry per pair of cell rows (2l, 2l + 1).
 struct __align__(16) IpRowPair {
-  float2 sgi;   // sigma_y = (l + 1/2) Q / k - v - 1/2 of both rows
-  float2 nsgi;  // -sigma_y
-  float2 ty;    // tau_y h of both rows
-  int32_t v0, v1;  // level-2 row offset v Q of both rows
+  float4 sg;  // (sigma_y, sigma_y', -sigma_y, -sigma_y'), sigma_y = (l + 1/2) Q / k - v - 1/2
+  float4 ty;  // (tau_y h, tau_y' h, y0, y0'), y0 = by_lo + lambda_2 tau_y h: the row's share of beta_2
+  int2 v;     // (v Q, v' Q): level-2 row offsets
 };
 
 // Row pairs of the row table past the cell's last: a thread's R / 2 pairs
@@ -595,8 +594,9 @@ struct IpSmem {
   static constexpr size_t near_xy = 0;
   static constexpr size_t near_m = near_xy + sizeof(float4) * IP_NEAR_MAX;
   static constexpr size_t sub = near_m + sizeof(float2) * IP_NEAR_MAX;
-  static constexpr size_t rows = sub + sizeof(float4) * Q * Q * K2;
-  static constexpr size_t coef = rows + sizeof(IpRowPair) * (IP_KMAX_RAYS / 2 + IP_ROW_PAD);
+  static constexpr int nrow = IP_KMAX_RAYS / 2 + IP_ROW_PAD;
+  static constexpr size_t row_sg = sub + sizeof(float4) * Q * Q * K2;
+  static constexpr size_t coef = row_sg + sizeof(IpRowPair) * nrow;
   static constexpr size_t bytes = (coef + sizeof(float2) * K2 * IP_CB_STRIDE + 15) / 16 * 16;
 };
 
@@ -619,7 +619,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   float4* nxy_s = reinterpret_cast<float4*>(ip_smem + L::near_xy);
   float2* nm_s = reinterpret_cast<float2*>(ip_smem + L::near_m);
   float4* sub_s = reinterpret_cast<float4*>(ip_smem + L::sub);
-  IpRowPair* row_s = reinterpret_cast<IpRowPair*>(ip_smem + L::rows);
+  IpRowPair* row_s = reinterpret_cast<IpRowPair*>(ip_smem + L::row_sg);
   float2* cb_s = reinterpret_cast<float2*>(ip_smem + L::coef);
   __shared__ CellRec rec_s;
   __shared__ int blk_start[9], blk_off[10];
@@ -729,8 +729,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   static_assert(R <= 2 * IP_ROW_PAD, "row table padding");
   const int npair_cell = (int)((k + 1) >> 1) + R / 2;
   for (int pr = tid; pr < npair_cell; pr += blockDim.x) {
-    IpRowPair rp;
-    float tyv[2], sg[2];
+    float tyv[2], sg[2], y0[2];
     int vq[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -738,20 +737,20 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
       const float sv = __fmul_rn(__fadd_rn((float)l, 0.5f), __fmul_rn((float)Q, inv_k));
       const int v = min(__float2int_rd(sv), Q - 1);
       tyv[j] = __fmul_rn(fmaf((float)l, inv_k, fmaf(0.5f, inv_k, -0.5f)), hf);
+      y0[j] = __fmaf_rn(g.lam_s2, tyv[j], rec_s.by_lo);
       sg[j] = __fsub_rn(__fsub_rn(sv, (float)v), 0.5f);
       vq[j] = v * Q;
     }
-    rp.ty = make_float2(tyv[0], tyv[1]);
-    rp.sgi = make_float2(sg[0], sg[1]);
-    rp.nsgi = make_float2(-sg[0], -sg[1]);
-    rp.v0 = vq[0];
-    rp.v1 = vq[1];
-    row_s[pr] = rp;
+    row_s[pr].sg = make_float4(sg[0], sg[1], -sg[0], -sg[1]);
+    row_s[pr].ty = make_float4(tyv[0], tyv[1], y0[0], y0[1]);
+    row_s[pr].v = make_int2(vq[0], vq[1]);
   }
   __syncthreads();
 
   // base pixel of this cell for the 32-bit pixel test
   const int32_t rix = rec_s.ix, riy = rec_s.iy;
+  // the cell centre's beta (hi parts) in pixel units
+  const float bxs = __fmul_rn(rec_s.bx_hi, g.inv_sx), bys = __fmul_rn(rec_s.by_hi, g.inv_sy);
   const int n_corner = rec_s.n_corner;
   const unsigned lane_lt = (1u << lane) - 1u;
   // cell-local 32-bit lattice indices: columns [0, kx), rows [ylo, yhi); units
@@ -780,11 +779,13 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     // y accumulator: both reach beta whatever the near sum does and fail the
     // pixel test
     const float tx = cl < kx ? __fmul_rn(fmaf((float)cl, inv_k, c_tau), hf) : fnan;
-    const float2 TX = make_float2(tx, tx), SGR = make_float2(sgr, sgr);
+    const float x0 = __fmaf_rn(g.lam_s1, tx, rec_s.bx_lo);  // the column's share of beta_1
+    const float2 TX = make_float2(tx, tx), SGR = make_float2(sgr, sgr), X0 = make_float2(x0, x0);
     float2 TY[R / 2], NAX[R / 2], NAY[R / 2];
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
-      TY[i] = row_s[p0 + i].ty;
+      const float4 t = row_s[p0 + i].ty;
+      TY[i] = make_float2(t.x, t.y);
       NAX[i] = make_float2(0.f, 0.f);
       NAY[i] = make_float2(0.f, 0.f);
     }
@@ -829,9 +830,8 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
         bool aligned = true;  // no pair straddles a sub-cell row: uniform over the warp
 #pragma unroll
         for (int i = 0; i < HP; ++i) {
-          const IpRowPair* rp = row_s + p0 + h + i;
-          SG[i] = *reinterpret_cast<const float4*>(rp);
-          const int2 v = *reinterpret_cast<const int2*>(&rp->v0);
+          SG[i] = row_s[p0 + h + i].sg;
+          const int2 v = row_s[p0 + h + i].v;
           va[i] = (v.x + u) * K2;
           aligned = aligned && (v.x == v.y);
         }
@@ -858,7 +858,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
         } else {
           int vb[HP];
 #pragma unroll
-          for (int i = 0; i < HP; ++i) vb[i] = (row_s[p0 + h + i].v1 + u) * K2;
+          for (int i = 0; i < HP; ++i) vb[i] = (row_s[p0 + h + i].v.y + u) * K2;
 #pragma unroll
           for (int i = 0; i < HP; ++i) {
             const float4 ea = sub_s[va[i] + K2 - 1], eb = sub_s[vb[i] + K2 - 1];
@@ -884,8 +884,8 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
 #pragma unroll
         for (int i = 0; i < HP; ++i) {
           float qr[2] = {QR[i].x, QR[i].y}, qi[2] = {QI[i].x, QI[i].y};
-          const float2 ty = row_s[p0 + h + i].ty;
-          const float tyr[2] = {ty.x, ty.y};
+          const float4 t = row_s[p0 + h + i].ty;
+          const float tyr[2] = {t.x, t.y};
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
             for (int c = 0; c < n_corner; ++c) {
@@ -900,34 +900,28 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
           QI[i] = make_float2(qi[0], qi[1]);
         }
       }
-      // beta relative to the base pixel (centre + lambda tau h + L_local -
-      // alpha_near) in pixel units, then the pixel key of every ray (~0 where
-      // none)
+      // beta relative to the base pixel, (by_hi, by_hi) + ((x0, y0) + L_local -
+      // alpha_near), in pixel units, then the pixel key of every ray (~0
+      // where none)
       uint32_t key[2 * HP];
 #pragma unroll
       for (int i = 0; i < HP; ++i) {
-        const float2 ty = row_s[p0 + h + i].ty;
-        const float4 cx4 = make_float4(rec_s.bx_hi, rec_s.bx_hi, rec_s.bx_lo, rec_s.bx_lo);
-        const float4 cy4 = make_float4(rec_s.by_hi, rec_s.by_hi, rec_s.by_lo, rec_s.by_lo);
-        const float4 lm4 = make_float4(g.lam_s1, g.lam_s1, g.lam_s2, g.lam_s2);
-        const float4 is4 = make_float4(g.inv_sx, g.inv_sx, g.inv_sy, g.inv_sy);
-        const float2 B1 = __fadd2_rn(make_float2(cx4.x, cx4.y),
-                                     __fadd2_rn(__fadd2_rn(make_float2(cx4.z, cx4.w), NAX[h + i]),
-                                                __ffma2_rn(make_float2(lm4.x, lm4.y), TX, QR[i])));
-        const float2 B2 = __fadd2_rn(make_float2(cy4.x, cy4.y),
-                                     __fadd2_rn(__fadd2_rn(make_float2(cy4.z, cy4.w), NAY[h + i]),
-                                                __ffma2_rn(make_float2(lm4.z, lm4.w), ty, QI[i])));
-        const float2 T1 = __fmul2_rn(B1, make_float2(is4.x, is4.y));
-        const float2 T2 = __fmul2_rn(B2, make_float2(is4.z, is4.w));
+        const float4 t = row_s[p0 + h + i].ty;
+        const float2 y0 = make_float2(t.z, t.w);
+        const float2 SX = __fadd2_rn(X0, __fadd2_rn(NAX[h + i], QR[i]));
+        const float2 SY = __fadd2_rn(y0, __fadd2_rn(NAY[h + i], QI[i]));
+        const float2 T1 = __ffma2_rn(SX, make_float2(g.inv_sx, g.inv_sx), make_float2(bxs, bxs));
+        const float2 T2 = __ffma2_rn(SY, make_float2(g.inv_sy, g.inv_sy), make_float2(bys, bys));
         key[2 * i] = pixel_key(T1.x, T2.x, rix, riy, g.npix_x, g.npix_y);
         key[2 * i + 1] = pixel_key(T1.y, T2.y, rix, riy, g.npix_x, g.npix_y);
         if (MODE == IP_DUMP) {
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
             if (i0 + cl == want_i && j0 + rl0 + 2 * (h + i) + j == want_j) {
-              const float b1 = j ? B1.y : B1.x, b2 = j ? B2.y : B2.x;
-              a.beta_out[2 * work] = (g.src_x0 + (double)rix * g.sx) + (double)b1;
-              a.beta_out[2 * work + 1] = (g.src_y0 + (double)riy * g.sy) + (double)b2;
+              const double b1 = (double)rec_s.bx_hi + (double)(j ? SX.y : SX.x);
+              const double b2 = (double)rec_s.by_hi + (double)(j ? SY.y : SY.x);
+              a.beta_out[2 * work] = (g.src_x0 + (double)rix * g.sx) + b1;
+              a.beta_out[2 * work + 1] = (g.src_y0 + (double)riy * g.sy) + b2;
               if (a.pix_out) a.pix_out[work] = key[2 * i + j] != 0xFFFFFFFFu ? (int64_t)key[2 * i + j] : -1;
             }
           }
