@@ -1,9 +1,11 @@
 // irs_fft.cu -- complex 2-D FFTs of length 2^a 3^b for the far-field
 // convolution on the level-1 cell grid, in double-float arithmetic
-// (irs_df.cuh: 48-bit significands on the FP32 pipes).
+// (irs_df.cuh: 48-bit significands on the FP32 pipes; float4 elements) or in
+// FP32 (float2 elements).
 //
-// A CTA loads B lines of length L = 3^n3 2^n2 (B*L <= 9216 complex values,
-// 144 KB) into shared memory in mixed-radix digit-reversed order, runs n3
+// A CTA loads B lines of length L = 3^n3 2^n2 (144 KB of line buffer: 9216
+// double-float or 18432 FP32 complex values) into shared memory in mixed-radix
+// digit-reversed order, runs n3
 // radix-3 then n2 radix-2 in-place decimation-in-time stages with a twiddle
 // table W_L^t (t < L/2; W_L^(t + L/2) = -W_L^t) staged beside them, and writes
 // the lines back.  Rows are contiguous lines; columns are strided lines, loaded
@@ -37,24 +39,80 @@ __device__ __forceinline__ unsigned digit_pos(unsigned e, int n3, int n2, unsign
   return r3 + pow3 * (n2 > 0 ? (__brev(lo) >> (32 - n2)) : 0u);
 }
 
-// W_L^t for 0 <= t < L from the half table, conjugated for the inverse
-template <bool INV>
-__device__ __forceinline__ float4 tw_at(const float4* w, int t, int half) {
-  float4 v = t < half ? w[t] : w[t - half];
-  if (t >= half) v = make_float4(-v.x, -v.y, -v.z, -v.w);
-  if (INV) {
-    v.z = -v.z;
-    v.w = -v.w;
-  }
-  return v;
+// Complex arithmetic of the two element types: float4 is double-float
+// (re.hi, re.lo, im.hi, im.lo), float2 is FP32 (re, im).
+__device__ __forceinline__ float4 c_add(float4 a, float4 b) { return dfc_add(a, b); }
+__device__ __forceinline__ float4 c_sub(float4 a, float4 b) { return dfc_sub(a, b); }
+__device__ __forceinline__ float4 c_mul(float4 a, float4 b) { return dfc_mul(a, b); }
+__device__ __forceinline__ float4 c_neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+__device__ __forceinline__ float4 c_conj(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+__device__ __forceinline__ float4 c_half(float4 a) { return make_float4(0.5f * a.x, 0.5f * a.y, 0.5f * a.z, 0.5f * a.w); }
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 c_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 c_half(float2 a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
+
+template <class T> __device__ __forceinline__ T c_zero();
+template <> __device__ __forceinline__ float4 c_zero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ float2 c_zero<float2>() { return make_float2(0.f, 0.f); }
+
+// twiddle table entry in the element type (the table holds double-float)
+template <class T> __device__ __forceinline__ T tw_elem(float4 v);
+template <> __device__ __forceinline__ float4 tw_elem<float4>(float4 v) { return v; }
+template <> __device__ __forceinline__ float2 tw_elem<float2>(float4 v) { return make_float2(v.x, v.z); }
+
+// output scaling by a real factor
+__device__ __forceinline__ float4 c_scale(float4 a, double s) {
+  return dfc_scale(a, make_float2((float)s, (float)(s - (double)(float)s)));
+}
+__device__ __forceinline__ float2 c_scale(float2 a, double s) {
+  const float f = (float)s;
+  return make_float2(a.x * f, a.y * f);
 }
 
-template <bool INV>
-__global__ void __launch_bounds__(512) k_fft_lines(const float4* in, float4* out, FftLines d,
-                                                   const float4* __restrict__ tw) {
-  extern __shared__ float4 sm[];
-  float4* x = sm;                           // [B][L]
-  float4* w = sm + (size_t)d.B * d.L;       // [L/2]
+// Radix-3 butterfly on a and the twiddled p, q:
+// x0 = a + t1, x1,2 = a - t1/2 -+ i s3 (p - q) with t1 = p + q and
+// s3 = +-sqrt(3)/2 (the sign of the transform's exponent).
+__device__ __forceinline__ void radix3(float4 a, float4 p, float4 q, bool inv, float4& x0, float4& x1,
+                                       float4& x2) {
+  const float2 s3 = inv ? make_float2(-8.660253882e-01f, -1.554362505e-08f)
+                        : make_float2(8.660253882e-01f, 1.554362505e-08f);  // sqrt(3)/2 = hi + lo
+  const float4 t1 = dfc_add(p, q);
+  const float4 t2 = dfc_sub(a, c_half(t1));
+  const float4 dd = dfc_sub(p, q);
+  const float2 u = df_mul(s3, dfc_im(dd)), v = df_mul(s3, dfc_re(dd));  // s3 Im(dd), s3 Re(dd)
+  x0 = dfc_add(a, t1);
+  x1 = dfc_make(df_add(dfc_re(t2), u), df_sub(dfc_im(t2), v));
+  x2 = dfc_make(df_sub(dfc_re(t2), u), df_add(dfc_im(t2), v));
+}
+__device__ __forceinline__ void radix3(float2 a, float2 p, float2 q, bool inv, float2& x0, float2& x1,
+                                       float2& x2) {
+  const float s3 = inv ? -0.8660254038f : 0.8660254038f;
+  const float2 t1 = c_add(p, q);
+  const float2 t2 = c_sub(a, c_half(t1));
+  const float2 dd = c_sub(p, q);
+  const float u = s3 * dd.y, v = s3 * dd.x;
+  x0 = c_add(a, t1);
+  x1 = make_float2(t2.x + u, t2.y - v);
+  x2 = make_float2(t2.x - u, t2.y + v);
+}
+
+// W_L^t for 0 <= t < L from the half table, conjugated for the inverse
+template <bool INV, class T>
+__device__ __forceinline__ T tw_at(const T* w, int t, int half) {
+  T v = t < half ? w[t] : c_neg(w[t - half]);
+  return INV ? c_conj(v) : v;
+}
+
+template <bool INV, class T>
+__global__ void __launch_bounds__(512) k_fft_lines(const T* in, T* out, FftLines d, const float4* __restrict__ tw) {
+  extern __shared__ float4 sm_raw[];
+  T* x = reinterpret_cast<T*>(sm_raw);  // [B][L]
+  T* w = x + (size_t)d.B * d.L;         // [L/2]
   const int L = d.L, B = d.B, n3 = d.n3, n2 = d.n2, half_L = L / 2;
   unsigned pow3 = 1;
   for (int i = 0; i < n3; ++i) pow3 *= 3u;
@@ -62,7 +120,7 @@ __global__ void __launch_bounds__(512) k_fft_lines(const float4* in, float4* out
   const int64_t goff_in = (int64_t)blockIdx.y * d.in_grid_stride;
   const int64_t goff_out = (int64_t)blockIdx.y * d.out_grid_stride;
   const int nthr = blockDim.x;
-  for (int k = threadIdx.x; k < L / 2; k += nthr) w[k] = tw[k];
+  for (int k = threadIdx.x; k < L / 2; k += nthr) w[k] = tw_elem<T>(tw[k]);
   // load, digit-reversed
   for (int idx = threadIdx.x; idx < B * L; idx += nthr) {
     int b, e;
@@ -74,7 +132,7 @@ __global__ void __launch_bounds__(512) k_fft_lines(const float4* in, float4* out
       e = idx / B;
     }
     const int64_t line = line0 + b;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    T v = c_zero<T>();
     if (line < d.n_lines && e < d.in_len)
       v = in[goff_in + line * d.in_line_stride + (int64_t)e * d.in_elem_stride];
     x[b * L + digit_pos((unsigned)e, n3, n2, pow3)] = v;
@@ -83,24 +141,16 @@ __global__ void __launch_bounds__(512) k_fft_lines(const float4* in, float4* out
   int m_prev = 1;  // span of the sub-transforms done so far
   // radix-3 stages: y_q = sum_r (W_m^(j r) x_r) W_3^(q r);
   // W_3 = -1/2 -+ i sqrt(3)/2, the halving is exact
-  const float2 s3 = INV ? make_float2(-8.660253882e-01f, -1.554362505e-08f)
-                        : make_float2(8.660253882e-01f, 1.554362505e-08f);  // sqrt(3)/2 = hi + lo
   for (int s = 0; s < n3; ++s) {
     const int m = m_prev * 3, stride = L / m;
     for (int t = threadIdx.x; t < B * (L / 3); t += nthr) {
       const int b = t / (L / 3), k = t % (L / 3);
       const int j = k % m_prev;
       const int i0 = (k / m_prev) * m + j, i1 = i0 + m_prev, i2 = i1 + m_prev;
-      const float4 a = x[b * L + i0];
-      const float4 p = dfc_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
-      const float4 q = dfc_mul(x[b * L + i2], tw_at<INV>(w, 2 * j * stride, half_L));
-      const float4 t1 = dfc_add(p, q);
-      const float4 t2 = dfc_sub(a, make_float4(0.5f * t1.x, 0.5f * t1.y, 0.5f * t1.z, 0.5f * t1.w));
-      const float4 dd = dfc_sub(p, q);
-      const float2 u = df_mul(s3, dfc_im(dd)), v = df_mul(s3, dfc_re(dd));  // s3 Im(dd), s3 Re(dd)
-      x[b * L + i0] = dfc_add(a, t1);
-      x[b * L + i1] = dfc_make(df_add(dfc_re(t2), u), df_sub(dfc_im(t2), v));
-      x[b * L + i2] = dfc_make(df_sub(dfc_re(t2), u), df_add(dfc_im(t2), v));
+      const T a = x[b * L + i0];
+      const T p = c_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
+      const T q = c_mul(x[b * L + i2], tw_at<INV>(w, 2 * j * stride, half_L));
+      radix3(a, p, q, INV, x[b * L + i0], x[b * L + i1], x[b * L + i2]);
     }
     __syncthreads();
     m_prev = m;
@@ -112,16 +162,15 @@ __global__ void __launch_bounds__(512) k_fft_lines(const float4* in, float4* out
       const int b = t / (L / 2), k = t % (L / 2);
       const int j = k % m_prev;
       const int i0 = (k / m_prev) * m + j, i1 = i0 + m_prev;
-      const float4 u = x[b * L + i0];
-      const float4 v = dfc_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
-      x[b * L + i0] = dfc_add(u, v);
-      x[b * L + i1] = dfc_sub(u, v);
+      const T u = x[b * L + i0];
+      const T v = c_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
+      x[b * L + i0] = c_add(u, v);
+      x[b * L + i1] = c_sub(u, v);
     }
     __syncthreads();
     m_prev = m;
   }
   const bool scaled = d.scale != 1.0;
-  const float2 sc = make_float2((float)d.scale, (float)(d.scale - (double)(float)d.scale));
   for (int idx = threadIdx.x; idx < B * L; idx += nthr) {
     int b, e;
     if (d.out_elem_stride == 1) {
@@ -133,8 +182,8 @@ __global__ void __launch_bounds__(512) k_fft_lines(const float4* in, float4* out
     }
     const int64_t line = line0 + b;
     if (line < d.n_lines && e < d.out_len) {
-      float4 v = x[b * L + e];
-      if (scaled) v = dfc_scale(v, sc);
+      T v = x[b * L + e];
+      if (scaled) v = c_scale(v, d.scale);
       out[goff_out + line * d.out_line_stride + (int64_t)e * d.out_elem_stride] = v;
     }
   }
@@ -178,66 +227,102 @@ cudaError_t fft_twiddles(int L, float4** d_tw) {
 
 cudaError_t fft_setup_attributes() {
   const int max_smem = (int)(FFT_MAX_ELEMS * sizeof(float4) + FFT_MAX_LEN / 2 * sizeof(float4));
-  cudaError_t e = cudaFuncSetAttribute(k_fft_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fft_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_lines<false, float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft_lines<true, float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft_lines<false, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft_lines<true, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  return e;
 }
 
-cudaError_t fft_lines(const float4* in, float4* out, FftLines d, int ngrids, const float4* tw,
-                      bool inverse, cudaStream_t s) {
+namespace {
+
+template <class T>
+cudaError_t fft_lines_t(const T* in, T* out, FftLines d, int ngrids, const float4* tw, bool inverse,
+                        cudaStream_t s) {
   if (d.n_lines <= 0 || ngrids <= 0) return cudaSuccess;
   const int64_t blocks = (d.n_lines + d.B - 1) / d.B;
-  const size_t smem = (size_t)d.B * d.L * sizeof(float4) + (size_t)(d.L / 2) * sizeof(float4);
+  const size_t smem = (size_t)d.B * d.L * sizeof(T) + (size_t)(d.L / 2) * sizeof(T);
   const int threads = d.B * d.L / 2 >= 512 ? 512 : (d.B * d.L / 2 >= 32 ? d.B * d.L / 2 : 32);
   dim3 grid((unsigned)blocks, (unsigned)ngrids);
   if (inverse)
-    k_fft_lines<true><<<grid, threads, smem, s>>>(in, out, d, tw);
+    k_fft_lines<true, T><<<grid, threads, smem, s>>>(in, out, d, tw);
   else
-    k_fft_lines<false><<<grid, threads, smem, s>>>(in, out, d, tw);
+    k_fft_lines<false, T><<<grid, threads, smem, s>>>(in, out, d, tw);
   return cudaGetLastError();
 }
 
-// Lines per CTA for a line length L: fill the shared line buffer.
-static int lines_per_cta(int L) {
-  int B = FFT_MAX_ELEMS / L;
+// Lines per CTA for a line length L: fill the shared line buffer (the same
+// bytes for both element types).
+template <class T>
+int lines_per_cta(int L) {
+  int B = (int)(FFT_MAX_ELEMS * sizeof(float4) / sizeof(T)) / L;
   return B < 1 ? 1 : (B > 16 ? 16 : B);
 }
 
-cudaError_t fft2d_forward(const float4* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
-                          float4* spec, const Fft2d& f, int ngrids, cudaStream_t s) {
+template <class T>
+cudaError_t fft2d_forward_t(const T* compact, int64_t nx, int64_t ny, int64_t in_grid_stride, T* spec,
+                            const Fft2d& f, int ngrids, cudaStream_t s) {
   // rows: compact rows [0, ny) -> spectrum rows, zero-padded to Nx
   FftLines r{};
-  r.L = f.Nx; r.n3 = f.n3x; r.n2 = f.n2x; r.B = lines_per_cta(f.Nx);
+  r.L = f.Nx; r.n3 = f.n3x; r.n2 = f.n2x; r.B = lines_per_cta<T>(f.Nx);
   r.n_lines = ny; r.in_len = (int)nx; r.out_len = f.Nx;
   r.in_line_stride = nx; r.in_elem_stride = 1; r.out_line_stride = f.Nx; r.out_elem_stride = 1;
   r.in_grid_stride = in_grid_stride; r.out_grid_stride = (int64_t)f.Nx * f.Ny; r.scale = 1.0;
-  cudaError_t e = fft_lines(compact, spec, r, ngrids, f.tw_x, false, s);
+  cudaError_t e = fft_lines_t(compact, spec, r, ngrids, f.tw_x, false, s);
   if (e != cudaSuccess) return e;
   // columns: all Nx, rows >= ny read as zero
   FftLines c{};
-  c.L = f.Ny; c.n3 = f.n3y; c.n2 = f.n2y; c.B = lines_per_cta(f.Ny);
+  c.L = f.Ny; c.n3 = f.n3y; c.n2 = f.n2y; c.B = lines_per_cta<T>(f.Ny);
   c.n_lines = f.Nx; c.in_len = (int)ny; c.out_len = f.Ny;
   c.in_line_stride = 1; c.in_elem_stride = f.Nx; c.out_line_stride = 1; c.out_elem_stride = f.Nx;
   c.in_grid_stride = (int64_t)f.Nx * f.Ny; c.out_grid_stride = (int64_t)f.Nx * f.Ny; c.scale = 1.0;
-  return fft_lines(spec, spec, c, ngrids, f.tw_y, false, s);
+  return fft_lines_t(spec, spec, c, ngrids, f.tw_y, false, s);
 }
 
-cudaError_t fft2d_inverse(float4* spec, const Fft2d& f, int64_t nx, int64_t ny, float4* compact,
-                          int64_t out_grid_stride, int ngrids, cudaStream_t s) {
+template <class T>
+cudaError_t fft2d_inverse_t(T* spec, const Fft2d& f, int64_t nx, int64_t ny, T* compact, int64_t out_grid_stride,
+                            int ngrids, cudaStream_t s) {
   FftLines c{};
-  c.L = f.Ny; c.n3 = f.n3y; c.n2 = f.n2y; c.B = lines_per_cta(f.Ny);
+  c.L = f.Ny; c.n3 = f.n3y; c.n2 = f.n2y; c.B = lines_per_cta<T>(f.Ny);
   c.n_lines = f.Nx; c.in_len = f.Ny; c.out_len = (int)ny;
   c.in_line_stride = 1; c.in_elem_stride = f.Nx; c.out_line_stride = 1; c.out_elem_stride = f.Nx;
   c.in_grid_stride = (int64_t)f.Nx * f.Ny; c.out_grid_stride = (int64_t)f.Nx * f.Ny; c.scale = 1.0;
-  cudaError_t e = fft_lines(spec, spec, c, ngrids, f.tw_y, true, s);
+  cudaError_t e = fft_lines_t(spec, spec, c, ngrids, f.tw_y, true, s);
   if (e != cudaSuccess) return e;
   FftLines r{};
-  r.L = f.Nx; r.n3 = f.n3x; r.n2 = f.n2x; r.B = lines_per_cta(f.Nx);
+  r.L = f.Nx; r.n3 = f.n3x; r.n2 = f.n2x; r.B = lines_per_cta<T>(f.Nx);
   r.n_lines = ny; r.in_len = f.Nx; r.out_len = (int)nx;
   r.in_line_stride = f.Nx; r.in_elem_stride = 1; r.out_line_stride = nx; r.out_elem_stride = 1;
   r.in_grid_stride = (int64_t)f.Nx * f.Ny; r.out_grid_stride = out_grid_stride;
   r.scale = 1.0;
-  return fft_lines(spec, compact, r, ngrids, f.tw_x, true, s);
+  return fft_lines_t(spec, compact, r, ngrids, f.tw_x, true, s);
+}
+
+}  // namespace
+
+cudaError_t fft_lines(const float4* in, float4* out, FftLines d, int ngrids, const float4* tw, bool inverse,
+                      cudaStream_t s) {
+  return fft_lines_t(in, out, d, ngrids, tw, inverse, s);
+}
+
+cudaError_t fft2d_forward(const float4* compact, int64_t nx, int64_t ny, int64_t in_grid_stride, float4* spec,
+                          const Fft2d& f, int ngrids, cudaStream_t s) {
+  return fft2d_forward_t(compact, nx, ny, in_grid_stride, spec, f, ngrids, s);
+}
+cudaError_t fft2d_forward(const float2* compact, int64_t nx, int64_t ny, int64_t in_grid_stride, float2* spec,
+                          const Fft2d& f, int ngrids, cudaStream_t s) {
+  return fft2d_forward_t(compact, nx, ny, in_grid_stride, spec, f, ngrids, s);
+}
+cudaError_t fft2d_inverse(float4* spec, const Fft2d& f, int64_t nx, int64_t ny, float4* compact,
+                          int64_t out_grid_stride, int ngrids, cudaStream_t s) {
+  return fft2d_inverse_t(spec, f, nx, ny, compact, out_grid_stride, ngrids, s);
+}
+cudaError_t fft2d_inverse(float2* spec, const Fft2d& f, int64_t nx, int64_t ny, float2* compact,
+                          int64_t out_grid_stride, int ngrids, cudaStream_t s) {
+  return fft2d_inverse_t(spec, f, nx, ny, compact, out_grid_stride, ngrids, s);
 }
 
 }  // namespace irs

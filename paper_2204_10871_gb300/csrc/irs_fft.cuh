@@ -1,6 +1,6 @@
-// irs_fft.cuh -- complex double-float FFTs of length 2^a 3^b (a >= 1) in shared
-// memory (irs_fft.cu).  Values are float4 (re.hi, re.lo, im.hi, im.lo), see
-// irs_df.cuh.
+// irs_fft.cuh -- complex FFTs of length 2^a 3^b (a >= 1) in shared memory
+// (irs_fft.cu), in double-float arithmetic on float4 values (re.hi, re.lo,
+// im.hi, im.lo; irs_df.cuh) or in FP32 on float2 values (re, im).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,8 +8,8 @@
 
 namespace irs {
 
-constexpr int FFT_MAX_ELEMS = 9216;  // complex values per CTA line buffer (144 KB; with the
-                                     // 72 KB twiddle table 216 KB of shared memory)
+constexpr int FFT_MAX_ELEMS = 9216;  // double-float complex values per CTA line buffer (144 KB;
+                                     // with the 72 KB twiddle table 216 KB of shared memory)
 constexpr int FFT_MAX_LEN = 9216;    // longest line (3^2 2^10)
 
 // One batched pass of 1-D FFTs over `n_lines` lines of length L.
@@ -40,9 +40,13 @@ cudaError_t fft_lines(const float4* in, float4* out, FftLines d, int ngrids, con
 // compact [ngrids][ny][nx] -> padded spectra [ngrids][Ny][Nx]
 cudaError_t fft2d_forward(const float4* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
                           float4* spec, const Fft2d& f, int ngrids, cudaStream_t s);
+cudaError_t fft2d_forward(const float2* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
+                          float2* spec, const Fft2d& f, int ngrids, cudaStream_t s);
 // padded spectra (overwritten) -> compact [ngrids][ny][nx], unnormalised (the
 // 1/(Nx Ny) is the caller's)
 cudaError_t fft2d_inverse(float4* spec, const Fft2d& f, int64_t nx, int64_t ny, float4* compact,
+                          int64_t out_grid_stride, int ngrids, cudaStream_t s);
+cudaError_t fft2d_inverse(float2* spec, const Fft2d& f, int64_t nx, int64_t ny, float2* compact,
                           int64_t out_grid_stride, int ngrids, cudaStream_t s);
 
 }  // namespace irs

@@ -45,6 +45,19 @@ constexpr int IP_KMAX = 32;        // local series terms (max)
 constexpr int IP_P = 18;           // multipole terms per cell
 constexpr int IP_KF = 14;          // local terms produced by the M2L (cells >= 4 apart:
                                    // truncation (0.71 / 3.29)^14 ~ 5e-10 of a cell's field)
+// Precision split of the convolution.  Multipole order j reaches the local
+// term k through kernels of order j + k, each cell >= 4 cells away, so its
+// share of term k is at most (0.71 / 4)^j = 0.18^j of the monopole's; local
+// term k moves a ray by at most 0.71^k times its value.  Only the low orders
+// carry sums that FP32 cannot hold to 1e-7 theta_E (term 0 is a potential-like
+// sum over the whole plane, term 1 grows with its logarithm): multipole
+// planes j < IP_PD and local planes k < IP_KD, with the kernel planes their
+// products need, are transformed and multiplied in double-float; every other
+// plane and product in FP32 (the j >= 4 share of term 0 is below 1e-3 of it,
+// so FP32 adds ~1e-10 relative; terms k >= 3 are stored as FP32 anyway).
+constexpr int IP_PD = 4;
+constexpr int IP_KD = 3;
+constexpr int IP_NKD = IP_PD + IP_KD - 1;  // kernel orders n = j + k of the double-float products
 constexpr int IP_NEAR_MAX = 1024;  // lenses of a 3x3 block held in shared memory
 constexpr int IP_KMAX_RAYS = 1024;  // rays along a cell side (row table in shared memory)
 constexpr int IP_THREADS = 256;
@@ -93,11 +106,16 @@ struct InterpState {
   float4* lens_rel;
   double2* lens_pos;
   double* lens_m;
-  // far-field convolution, complex double-float (irs_df.cuh)
-  float4* mpole;  // [P][ncells]
-  float4* spec;   // [P][Ny][Nx]
-  float4* kspec;  // [P+KF-1][Ny][Nx], normalised by 1/(Nx Ny)
-  float4* conv;   // [KF][ncells]
+  // far-field convolution: complex double-float (float4, irs_df.cuh) for
+  // the low orders, FP32 (float2) for the rest
+  float4* mpole_d;  // [PD][ncells]    multipoles j < PD
+  float2* mpole_f;  // [P-PD][ncells]  multipoles j >= PD
+  float4* spec_d;   // [PD][Ny][Nx]    their spectra; then local spectra k < KD
+  float2* spec_f;   // [P-PD][Ny][Nx]  their spectra; then local spectra KD <= k < KF
+  float4* kspec_d;  // [NKD][Ny][Nx]   kernel spectra n < NKD, normalised by 1/(Nx Ny)
+  float2* kspec_f;  // [P+KF-1][Ny][Nx] every kernel spectrum in FP32
+  float4* conv_d;   // [KD][ncells]    local terms k < KD
+  float2* conv_f;   // [KF-KD][ncells] local terms KD <= k < KF
   CellRec* recs;   // [nray cells]
   float2* coef;    // [nray cells][K]
   int grid_ray;
@@ -216,7 +234,8 @@ __global__ void k_ip_fill(IpGeo ig, const double2* __restrict__ xy, const double
 // ------------------------------------------------------------ far field
 // P2M: a_j = sum_i m_i ((z_i - z_S)/h)^j for the lenses of cell S.
 __global__ void k_ip_p2m(IpGeo ig, const int32_t* __restrict__ start, const double2* __restrict__ pos,
-                         const double* __restrict__ m, float4* __restrict__ mpole) {
+                         const double* __restrict__ m, float4* __restrict__ mpole_d,
+                         float2* __restrict__ mpole_f) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ncells = (int64_t)ig.ncx * ig.ncy;
   if (c >= ncells) return;
@@ -237,15 +256,22 @@ __global__ void k_ip_p2m(IpGeo ig, const int32_t* __restrict__ start, const doub
     }
   }
 #pragma unroll
-  for (int j = 0; j < IP_P; ++j) mpole[(int64_t)j * ncells + c] = dfc_from_double(a[j].re, a[j].im);
+  for (int j = 0; j < IP_P; ++j) {
+    if (j < IP_PD)
+      mpole_d[(int64_t)j * ncells + c] = dfc_from_double(a[j].re, a[j].im);
+    else
+      mpole_f[(int64_t)(j - IP_PD) * ncells + c] = make_float2((float)a[j].re, (float)a[j].im);
+  }
 }
 
 // Translation kernels on the padded grid, scaled by n! / (Nx Ny):
 // K'_n[e] = n! (-e)^-(n+1) / (Nx Ny) for offsets e (cell units, wrapped) with
 // Chebyshev norm > W, else 0 (the n! is one factor of the M2L's binomial,
 // below; the 1/(Nx Ny) normalises the inverse FFT and keeps every spectrum
-// far inside the FP32 exponent range of the double-float convolution).
-__global__ void k_ip_kernel_grid(int Nx, int Ny, int W, int nker, float4* __restrict__ kg) {
+// far inside the FP32 exponent range).  Orders n < nkd in double-float (kg_d),
+// every order in FP32 (kg_f).
+__global__ void k_ip_kernel_grid(int Nx, int Ny, int W, int nker, int nkd, float4* __restrict__ kg_d,
+                                 float2* __restrict__ kg_f) {
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t G = (int64_t)Nx * Ny;
   if (f >= G) return;
@@ -258,44 +284,72 @@ __global__ void k_ip_kernel_grid(int Nx, int Ny, int W, int nker, float4* __rest
   double fact = 1.0 / (double)G;  // n! / (Nx Ny)
   for (int n = 0; n < nker; ++n) {
     if (n > 0) fact *= (double)n;
-    kg[(int64_t)n * G + f] = far ? dfc_from_double(pw.re * fact, pw.im * fact) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const double re = far ? pw.re * fact : 0.0, im = far ? pw.im * fact : 0.0;
+    if (n < nkd) kg_d[(int64_t)n * G + f] = dfc_from_double(re, im);
+    kg_f[(int64_t)n * G + f] = make_float2((float)re, (float)im);
     pw = cmul(pw, inv);
   }
 }
 
-// Pointwise M2L in frequency space, in double-float:
+// Pointwise M2L in frequency space:
 //   C_k = sum_j (-1)^j binom(j+k, k) A_j Kh_{j+k},  j < P, k < KF,
 // with binom(j+k, k) = (j+k)! / (j! k!): the (j+k)! sits in the kernel
 // spectra, so each term is one complex multiply-add of (-1)^j A_j / j! and
-// the scaled kernel, and C_k takes the 1/k! at the end.
-__global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, float4* __restrict__ spec,
-                                                     const float4* __restrict__ kspec) {
+// the scaled kernel, and C_k takes the 1/k! at the end.  Products with
+// j < PD and k < KD in double-float, the others in FP32 (the FP32 operands
+// of the double-float planes are their high parts); the FP32 share of
+// C_k, k < KD, joins the double-float sum before the scaling.
+__global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, float4* __restrict__ spec_d,
+                                                     float2* __restrict__ spec_f,
+                                                     const float4* __restrict__ kspec_d,
+                                                     const float2* __restrict__ kspec_f) {
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= G) return;
-  float4 A[IP_P], Cc[IP_KF];
+  float4 Ad[IP_PD], Cd[IP_KD];
+  float2 Af[IP_P], Cf[IP_KF];
   double ifact = 1.0;  // 1/j!, folded at compile time
 #pragma unroll
   for (int j = 0; j < IP_P; ++j) {
     if (j > 0) ifact /= (double)j;
-    A[j] = dfc_scale(spec[(int64_t)j * G + f], df_from_double(((j & 1) ? -1.0 : 1.0) * ifact));
+    const double sc = ((j & 1) ? -1.0 : 1.0) * ifact;
+    if (j < IP_PD) {
+      Ad[j] = dfc_scale(spec_d[(int64_t)j * G + f], df_from_double(sc));
+      Af[j] = make_float2(Ad[j].x, Ad[j].z);
+    } else {
+      const float2 v = spec_f[(int64_t)(j - IP_PD) * G + f];
+      Af[j] = make_float2(v.x * (float)sc, v.y * (float)sc);
+    }
   }
 #pragma unroll
-  for (int k = 0; k < IP_KF; ++k) Cc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = 0; k < IP_KD; ++k) Cd[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < IP_KF; ++k) Cf[k] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int nn = 0; nn < IP_P + IP_KF - 1; ++nn) {
-    const float4 kv = kspec[(int64_t)nn * G + f];
+    const float2 kf = kspec_f[(int64_t)nn * G + f];
+    const float4 kd = nn < IP_NKD ? kspec_d[(int64_t)nn * G + f] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < IP_P; ++j) {
       const int k = nn - j;
       if (k < 0 || k >= IP_KF) continue;
-      Cc[k] = dfc_add(Cc[k], dfc_mul(A[j], kv));
+      if (j < IP_PD && k < IP_KD) {
+        Cd[k] = dfc_add(Cd[k], dfc_mul(Ad[j], kd));
+      } else {
+        Cf[k].x = fmaf(Af[j].x, kf.x, fmaf(-Af[j].y, kf.y, Cf[k].x));
+        Cf[k].y = fmaf(Af[j].x, kf.y, fmaf(Af[j].y, kf.x, Cf[k].y));
+      }
     }
   }
   double kfact = 1.0;  // 1/k!
 #pragma unroll
   for (int k = 0; k < IP_KF; ++k) {
     if (k > 0) kfact /= (double)k;
-    spec[(int64_t)k * G + f] = dfc_scale(Cc[k], df_from_double(kfact));
+    if (k < IP_KD) {
+      const float4 c = dfc_add(Cd[k], make_float4(Cf[k].x, 0.f, Cf[k].y, 0.f));
+      spec_d[(int64_t)k * G + f] = dfc_scale(c, df_from_double(kfact));
+    } else {
+      spec_f[(int64_t)(k - IP_KD) * G + f] = make_float2(Cf[k].x * (float)kfact, Cf[k].y * (float)kfact);
+    }
   }
 }
 
@@ -308,6 +362,7 @@ __global__ void __launch_bounds__(128) k_ip_m2l_freq(int64_t G, float4* __restri
 // beta, and the two largest slopes) keep FP64.
 constexpr int FIN_K64 = 3;
 constexpr int FIN_K32 = IP_KMAX - FIN_K64;
+static_assert(IP_KD >= FIN_K64, "FP32 local planes feed only FP32 accumulators");
 
 // 1/a for complex a, |a| >~ 1e-19 (cell or theta_E units): an FP32 seed for
 // 1/|a|^2 refined by one FP64 Newton step (relative error ~1e-14), instead of
@@ -327,8 +382,8 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 // term, base pixel.
 __global__ void __launch_bounds__(64)
 k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* __restrict__ start,
-              const double2* __restrict__ pos, const double* __restrict__ m, const float4* __restrict__ conv,
-              MlpFar far, CellRec* __restrict__ recs, float2* __restrict__ coef, int64_t rc0, int64_t rc1) {
+              const double2* __restrict__ pos, const double* __restrict__ m, const float4* __restrict__ conv_d,
+              const float2* __restrict__ conv_f, MlpFar far, CellRec* __restrict__ recs, float2* __restrict__ coef, int64_t rc0, int64_t rc1) {
   const int64_t rc = rc0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (rc >= rc1) return;
   const int cx = (int)(rc % ig.nrcx) + ig.ox, cy = (int)(rc / ig.nrcx) + ig.oy;
@@ -388,13 +443,19 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
 #pragma unroll
     for (int k = 0; k < IP_KF; ++k) {
       if (k >= K) break;
-      const float4 v = conv[(int64_t)k * ncells + c];
-      if (k < FIN_K64) {
-        acc[k].re += df_to_double(dfc_re(v));
-        acc[k].im += df_to_double(dfc_im(v));
+      if (k < IP_KD) {
+        const float4 v = conv_d[(int64_t)k * ncells + c];
+        if (k < FIN_K64) {
+          acc[k].re += df_to_double(dfc_re(v));
+          acc[k].im += df_to_double(dfc_im(v));
+        } else {
+          accf[k - FIN_K64].x += v.x + v.y;
+          accf[k - FIN_K64].y += v.z + v.w;
+        }
       } else {
-        accf[k - FIN_K64].x += v.x + v.y;
-        accf[k - FIN_K64].y += v.z + v.w;
+        const float2 v = conv_f[(int64_t)(k - IP_KD) * ncells + c];
+        accf[k - FIN_K64].x += v.x;
+        accf[k - FIN_K64].y += v.y;
       }
     }
   }
@@ -1138,20 +1199,24 @@ irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* ma
     irs_status st = mlp_prepare(P, xy, mass, n, ig.gx0, ig.gy0, ig.h, ig.nrcx, ig.nrcy, ig.ox, ig.oy, &far, s);
     if (st != IRS_OK) return st;
   } else {
-    k_ip_p2m<<<(unsigned)((ncells + 127) / 128), 128, 0, s>>>(ig, S->cell_start, S->lens_pos, S->lens_m, S->mpole);
+    k_ip_p2m<<<(unsigned)((ncells + 127) / 128), 128, 0, s>>>(ig, S->cell_start, S->lens_pos, S->lens_m,
+                                                             S->mpole_d, S->mpole_f);
     IP_TRY(cudaGetLastError());
-    IP_TRY(fft2d_forward(S->mpole, ig.ncx, ig.ncy, ncells, S->spec, S->fft, ig.P, s));
+    IP_TRY(fft2d_forward(S->mpole_d, ig.ncx, ig.ncy, ncells, S->spec_d, S->fft, IP_PD, s));
+    IP_TRY(fft2d_forward(S->mpole_f, ig.ncx, ig.ncy, ncells, S->spec_f, S->fft, IP_P - IP_PD, s));
     const int64_t G = (int64_t)S->fft.Nx * S->fft.Ny;
-    k_ip_m2l_freq<<<(unsigned)((G + 127) / 128), 128, 0, s>>>(G, S->spec, S->kspec);
+    k_ip_m2l_freq<<<(unsigned)((G + 127) / 128), 128, 0, s>>>(G, S->spec_d, S->spec_f, S->kspec_d, S->kspec_f);
     IP_TRY(cudaGetLastError());
-    IP_TRY(fft2d_inverse(S->spec, S->fft, ig.ncx, ig.ncy, S->conv, ncells, IP_KF, s));
+    IP_TRY(fft2d_inverse(S->spec_d, S->fft, ig.ncx, ig.ncy, S->conv_d, ncells, IP_KD, s));
+    IP_TRY(fft2d_inverse(S->spec_f, S->fft, ig.ncx, ig.ncy, S->conv_f, ncells, IP_KF - IP_KD, s));
   }
   const int64_t nrc = (int64_t)ig.nrcx * ig.nrcy;
   if (rc1 < 0 || rc1 > nrc) rc1 = nrc;
   mark(P, EV_FIN, s);
   if (rc1 > rc0)
     k_ip_finalize<<<(unsigned)((rc1 - rc0 + 63) / 64), 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start,
-                                                                   S->lens_pos, S->lens_m, S->conv, far,
+                                                                   S->lens_pos, S->lens_m, S->conv_d,
+                                                                   S->conv_f, far,
                                                                    S->recs, S->coef, rc0, rc1);
   IP_TRY(cudaGetLastError());
   mark(P, EV_FAR, s);
@@ -1246,8 +1311,11 @@ irs_status interp_plan(irs_plan_t* P) {
   const size_t o_cnt = take(sizeof(int32_t) * ncells), o_start = take(sizeof(int32_t) * (ncells + 1));
   const size_t o_cur = take(sizeof(int32_t) * ncells);
   const size_t o_sb = take(sizeof(int32_t) * ((ncells + SCAN_B - 1) / SCAN_B + 1));
-  const size_t o_mp = take(sizeof(float4) * ig.P * ncells), o_conv = take(sizeof(float4) * IP_KF * ncells);
-  const size_t o_spec = take(sizeof(float4) * ig.P * G), o_kspec = take(sizeof(float4) * (ig.P + IP_KF - 1) * G);
+  static_assert(IP_KD <= IP_PD && IP_KF - IP_KD <= IP_P - IP_PD, "local spectra overwrite multipole spectra");
+  const size_t o_mpd = take(sizeof(float4) * IP_PD * ncells), o_mpf = take(sizeof(float2) * (IP_P - IP_PD) * ncells);
+  const size_t o_cvd = take(sizeof(float4) * IP_KD * ncells), o_cvf = take(sizeof(float2) * (IP_KF - IP_KD) * ncells);
+  const size_t o_spd = take(sizeof(float4) * IP_PD * G), o_spf = take(sizeof(float2) * (IP_P - IP_PD) * G);
+  const size_t o_ksd = take(sizeof(float4) * IP_NKD * G), o_ksf = take(sizeof(float2) * (IP_P + IP_KF - 1) * G);
   const size_t o_rec = take(sizeof(CellRec) * nrc), o_coef = take(sizeof(float2) * ig.K * nrc);
   if (cudaMalloc(&S->ws, off) != cudaSuccess) {
     cudaGetLastError();
@@ -1260,19 +1328,24 @@ irs_status interp_plan(irs_plan_t* P) {
   S->cell_start = reinterpret_cast<int32_t*>(b + o_start);
   S->cell_cursor = reinterpret_cast<int32_t*>(b + o_cur);
   S->scan_blocks = reinterpret_cast<int32_t*>(b + o_sb);
-  S->mpole = reinterpret_cast<float4*>(b + o_mp);
-  S->conv = reinterpret_cast<float4*>(b + o_conv);
-  S->spec = reinterpret_cast<float4*>(b + o_spec);
-  S->kspec = reinterpret_cast<float4*>(b + o_kspec);
+  S->mpole_d = reinterpret_cast<float4*>(b + o_mpd);
+  S->mpole_f = reinterpret_cast<float2*>(b + o_mpf);
+  S->conv_d = reinterpret_cast<float4*>(b + o_cvd);
+  S->conv_f = reinterpret_cast<float2*>(b + o_cvf);
+  S->spec_d = reinterpret_cast<float4*>(b + o_spd);
+  S->spec_f = reinterpret_cast<float2*>(b + o_spf);
+  S->kspec_d = reinterpret_cast<float4*>(b + o_ksd);
+  S->kspec_f = reinterpret_cast<float2*>(b + o_ksf);
   S->recs = reinterpret_cast<CellRec*>(b + o_rec);
   S->coef = reinterpret_cast<float2*>(b + o_coef);
   irs_status st = alloc_lens_buffers(S, nstar + nstar / 4 + 256);
   if (st != IRS_OK) return st;
   // translation kernels and their spectra, once per plan
   const int nker = ig.P + IP_KF - 1;
-  k_ip_kernel_grid<<<(unsigned)((G + 255) / 256), 256>>>(f.Nx, f.Ny, ig.W, nker, S->kspec);
+  k_ip_kernel_grid<<<(unsigned)((G + 255) / 256), 256>>>(f.Nx, f.Ny, ig.W, nker, IP_NKD, S->kspec_d, S->kspec_f);
   if (cudaGetLastError() != cudaSuccess) return IRS_ERR_CUDA;
-  if (fft2d_forward(S->kspec, f.Nx, f.Ny, G, S->kspec, f, nker, 0) != cudaSuccess) return IRS_ERR_CUDA;
+  if (fft2d_forward(S->kspec_d, f.Nx, f.Ny, G, S->kspec_d, f, IP_NKD, 0) != cudaSuccess) return IRS_ERR_CUDA;
+  if (fft2d_forward(S->kspec_f, f.Nx, f.Ny, G, S->kspec_f, f, nker, 0) != cudaSuccess) return IRS_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return IRS_ERR_CUDA;
   if (ip_ray_attributes(ig.variant) != cudaSuccess) return IRS_ERR_CUDA;
   S->grid_ray = P->num_sms * ip_ray_occupancy(ig.variant);
