@@ -402,40 +402,45 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
 #pragma unroll
   for (int k = 0; k < FIN_K32; ++k) accf[k] = make_float2(0.f, 0.f);
   // direct ring: lenses of cells at Chebyshev distance 2..W (series mode), or
-  // every lens outside the near block weighted by w(r) out to R_f (network mode)
+  // every lens outside the near block weighted by w(r) out to R_f (network
+  // mode).  The (cell, lens) pairs are walked as one sequence per thread, one
+  // lens per step, so that the lanes of a warp, whose windows hold different
+  // numbers of lenses per cell, stay busy until their own lenses run out.
   const int Wd = far.active ? (int)ceil(far.rf) + 1 : ig.W;
-  for (int dy = -Wd; dy <= Wd; ++dy) {
-    const int y = cy + dy;
-    if (y < 0 || y >= ig.ncy) continue;
-    for (int dx = -Wd; dx <= Wd; ++dx) {
-      if (abs(dx) <= 1 && abs(dy) <= 1) continue;
-      const int x = cx + dx;
-      if (x < 0 || x >= ig.ncx) continue;
+  const int side = 2 * Wd + 1, nwin = side * side;
+  int q = -1, p = 0, pend = 0;  // window cell (row-major), lens range left in it
+  while (true) {
+    while (p >= pend && ++q < nwin) {
+      const int dy = q / side - Wd, dx = q % side - Wd;
+      const int x = cx + dx, y = cy + dy;
+      if ((abs(dx) <= 1 && abs(dy) <= 1) || x < 0 || x >= ig.ncx || y < 0 || y >= ig.ncy) continue;
       const int64_t s = (int64_t)y * ig.ncx + x;
-      for (int p = start[s]; p < start[s + 1]; ++p) {
-        const cd d = {(pos[p].x - zx) * inv_h, (pos[p].y - zy) * inv_h};
-        double wm = m[p];
-        if (far.active) {
-          wm *= mlp_ring_weight(hypot(d.re, d.im), far.rf);
-          if (wm == 0.0) continue;
-        }
-        const cd inv = crecip_nr(d);
-        cd pw = {wm * inv.re, wm * inv.im};  // + m d^-(k+1)
+      p = start[s];
+      pend = start[s + 1];
+    }
+    if (q >= nwin) break;
+    const int pl = p++;  // this step's lens (the step always advances)
+    const cd d = {(pos[pl].x - zx) * inv_h, (pos[pl].y - zy) * inv_h};
+    double wm = m[pl];
+    if (far.active) {
+      wm *= mlp_ring_weight(hypot(d.re, d.im), far.rf);
+      if (wm == 0.0) continue;
+    }
+    const cd inv = crecip_nr(d);
+    cd pw = {wm * inv.re, wm * inv.im};  // + m d^-(k+1)
 #pragma unroll
-        for (int k = 0; k < FIN_K64; ++k) {
-          acc[k].re += pw.re;
-          acc[k].im += pw.im;
-          pw = cmul(pw, inv);
-        }
-        const float2 invf = make_float2((float)inv.re, (float)inv.im);
-        float2 pf = make_float2((float)pw.re, (float)pw.im);
+    for (int k = 0; k < FIN_K64; ++k) {
+      acc[k].re += pw.re;
+      acc[k].im += pw.im;
+      pw = cmul(pw, inv);
+    }
+    const float2 invf = make_float2((float)inv.re, (float)inv.im);
+    float2 pf = make_float2((float)pw.re, (float)pw.im);
 #pragma unroll
-        for (int k = 0; k < FIN_K32; ++k) {
-          accf[k].x += pf.x;
-          accf[k].y += pf.y;
-          pf = cmulf(pf, invf);
-        }
-      }
+    for (int k = 0; k < FIN_K32; ++k) {
+      accf[k].x += pf.x;
+      accf[k].y += pf.y;
+      pf = cmulf(pf, invf);
     }
   }
   // outer cells through the FFT convolution (series mode)
