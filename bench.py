@@ -171,7 +171,7 @@ def ip_flops_fixed(variant):
 # dram__bytes_write.sum), valid only for the kernel build, workload and cell
 # size they were captured on: (workload, cell multiplier, variant) -> bytes.
 # Source: profiles/k_ip_ray_paper-mid-full.md.
-IP_TRAFFIC = {("paper-mid", 0.85, 0): 58.070016e6 + 76.544e3}
+IP_TRAFFIC = {("paper-mid", 0.57, 0): 106.746112e6 + 3.398912e6}
 
 
 def mean_near_lenses(info, xy):
