@@ -101,6 +101,15 @@ __device__ __forceinline__ void radix3(float2 a, float2 p, float2 q, bool inv, f
   x2 = make_float2(t2.x - u, t2.y + v);
 }
 
+// Quotient by a divisor d that is fixed for a loop: umulhi(x, ceil(2^32 / d))
+// equals floor(x / d) whenever x d < 2^32 (here x < 2^15 and d < 2^14), with
+// no division instruction sequence per element.
+struct FastDiv {
+  uint32_t d, m;
+  __device__ explicit FastDiv(uint32_t dv) : d(dv), m(dv > 1u ? 0xFFFFFFFFu / dv + 1u : 0u) {}
+  __device__ __forceinline__ uint32_t div(uint32_t x) const { return d > 1u ? __umulhi(x, m) : x; }
+};
+
 // W_L^t for 0 <= t < L from the half table, conjugated for the inverse
 template <bool INV, class T>
 __device__ __forceinline__ T tw_at(const T* w, int t, int half) {
@@ -120,16 +129,17 @@ __global__ void __launch_bounds__(512) k_fft_lines(const T* in, T* out, FftLines
   const int64_t goff_in = (int64_t)blockIdx.y * d.in_grid_stride;
   const int64_t goff_out = (int64_t)blockIdx.y * d.out_grid_stride;
   const int nthr = blockDim.x;
+  const FastDiv fdL((uint32_t)L), fdB((uint32_t)B), fd3((uint32_t)(L / 3)), fd2((uint32_t)half_L);
   for (int k = threadIdx.x; k < L / 2; k += nthr) w[k] = tw_elem<T>(tw[k]);
   // load, digit-reversed
   for (int idx = threadIdx.x; idx < B * L; idx += nthr) {
     int b, e;
     if (d.in_elem_stride == 1) {
-      b = idx / L;
-      e = idx % L;
+      b = (int)fdL.div((uint32_t)idx);
+      e = idx - b * L;
     } else {
-      b = idx % B;
-      e = idx / B;
+      e = (int)fdB.div((uint32_t)idx);
+      b = idx - e * B;
     }
     const int64_t line = line0 + b;
     T v = c_zero<T>();
@@ -143,10 +153,11 @@ __global__ void __launch_bounds__(512) k_fft_lines(const T* in, T* out, FftLines
   // W_3 = -1/2 -+ i sqrt(3)/2, the halving is exact
   for (int s = 0; s < n3; ++s) {
     const int m = m_prev * 3, stride = L / m;
+    const FastDiv fdm((uint32_t)m_prev);
     for (int t = threadIdx.x; t < B * (L / 3); t += nthr) {
-      const int b = t / (L / 3), k = t % (L / 3);
-      const int j = k % m_prev;
-      const int i0 = (k / m_prev) * m + j, i1 = i0 + m_prev, i2 = i1 + m_prev;
+      const int b = (int)fd3.div((uint32_t)t), k = t - b * (L / 3);
+      const int g = (int)fdm.div((uint32_t)k), j = k - g * m_prev;
+      const int i0 = g * m + j, i1 = i0 + m_prev, i2 = i1 + m_prev;
       const T a = x[b * L + i0];
       const T p = c_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
       const T q = c_mul(x[b * L + i2], tw_at<INV>(w, 2 * j * stride, half_L));
@@ -158,10 +169,11 @@ __global__ void __launch_bounds__(512) k_fft_lines(const T* in, T* out, FftLines
   // radix-2 stages
   for (int s = 0; s < n2; ++s) {
     const int m = m_prev * 2, stride = L / m;
+    const FastDiv fdm((uint32_t)m_prev);
     for (int t = threadIdx.x; t < B * (L / 2); t += nthr) {
-      const int b = t / (L / 2), k = t % (L / 2);
-      const int j = k % m_prev;
-      const int i0 = (k / m_prev) * m + j, i1 = i0 + m_prev;
+      const int b = (int)fd2.div((uint32_t)t), k = t - b * half_L;
+      const int g = (int)fdm.div((uint32_t)k), j = k - g * m_prev;
+      const int i0 = g * m + j, i1 = i0 + m_prev;
       const T u = x[b * L + i0];
       const T v = c_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
       x[b * L + i0] = c_add(u, v);
@@ -174,11 +186,11 @@ __global__ void __launch_bounds__(512) k_fft_lines(const T* in, T* out, FftLines
   for (int idx = threadIdx.x; idx < B * L; idx += nthr) {
     int b, e;
     if (d.out_elem_stride == 1) {
-      b = idx / L;
-      e = idx % L;
+      b = (int)fdL.div((uint32_t)idx);
+      e = idx - b * L;
     } else {
-      b = idx % B;
-      e = idx / B;
+      e = (int)fdB.div((uint32_t)idx);
+      b = idx - e * B;
     }
     const int64_t line = line0 + b;
     if (line < d.n_lines && e < d.out_len) {
