@@ -266,11 +266,14 @@ cudaError_t fft_lines_t(const T* in, T* out, FftLines d, int ngrids, const float
   return cudaGetLastError();
 }
 
-// Lines per CTA for a line length L: fill the shared line buffer (the same
-// bytes for both element types).
+// Lines per CTA for a line length L: as many as keep the CTA's lines and
+// twiddle table within a quarter of the SM's shared memory, so that up to four
+// CTAs share an SM and hide each other's barriers; at least one line.
+constexpr size_t FFT_CTA_BYTES = 52 * 1024;
 template <class T>
 int lines_per_cta(int L) {
-  int B = (int)(FFT_MAX_ELEMS * sizeof(float4) / sizeof(T)) / L;
+  const size_t tw = (size_t)(L / 2) * sizeof(T), line = (size_t)L * sizeof(T);
+  int B = FFT_CTA_BYTES > tw ? (int)((FFT_CTA_BYTES - tw) / line) : 0;
   return B < 1 ? 1 : (B > 16 ? 16 : B);
 }
 
