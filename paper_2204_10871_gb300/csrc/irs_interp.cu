@@ -232,7 +232,9 @@ __global__ void k_ip_fill(IpGeo ig, const double2* __restrict__ xy, const double
 }
 
 // ------------------------------------------------------------ far field
-// P2M: a_j = sum_i m_i ((z_i - z_S)/h)^j for the lenses of cell S.
+// P2M: a_j = sum_i m_i ((z_i - z_S)/h)^j for the lenses of cell S; orders
+// j < IP_PD in FP64 (stored double-float), the rest in FP32 from the FP32
+// offset (|d| <= 0.71; they are stored and convolved in FP32).
 __global__ void k_ip_p2m(IpGeo ig, const int32_t* __restrict__ start, const double2* __restrict__ pos,
                          const double* __restrict__ m, float4* __restrict__ mpole_d,
                          float2* __restrict__ mpole_f) {
@@ -241,27 +243,35 @@ __global__ void k_ip_p2m(IpGeo ig, const int32_t* __restrict__ start, const doub
   if (c >= ncells) return;
   const int cx = (int)(c % ig.ncx), cy = (int)(c / ig.ncx);
   const double zx = ig.gx0 + (cx + 0.5) * ig.h, zy = ig.gy0 + (cy + 0.5) * ig.h;
-  cd a[IP_P];
+  cd a[IP_PD];
+  float2 af[IP_P - IP_PD];
 #pragma unroll
-  for (int j = 0; j < IP_P; ++j) a[j] = {0.0, 0.0};
+  for (int j = 0; j < IP_PD; ++j) a[j] = {0.0, 0.0};
+#pragma unroll
+  for (int j = 0; j < IP_P - IP_PD; ++j) af[j] = make_float2(0.f, 0.f);
   const double inv_h = 1.0 / ig.h;
   for (int p = start[c]; p < start[c + 1]; ++p) {
     const cd d = {(pos[p].x - zx) * inv_h, (pos[p].y - zy) * inv_h};
     cd pw = {m[p], 0.0};
 #pragma unroll
-    for (int j = 0; j < IP_P; ++j) {
+    for (int j = 0; j < IP_PD; ++j) {
       a[j].re += pw.re;
       a[j].im += pw.im;
       pw = cmul(pw, d);
     }
+    const float2 df = make_float2((float)d.re, (float)d.im);
+    float2 pf = make_float2((float)pw.re, (float)pw.im);  // m d^PD
+#pragma unroll
+    for (int j = 0; j < IP_P - IP_PD; ++j) {
+      af[j].x += pf.x;
+      af[j].y += pf.y;
+      pf = make_float2(fmaf(pf.x, df.x, -pf.y * df.y), fmaf(pf.x, df.y, pf.y * df.x));
+    }
   }
 #pragma unroll
-  for (int j = 0; j < IP_P; ++j) {
-    if (j < IP_PD)
-      mpole_d[(int64_t)j * ncells + c] = dfc_from_double(a[j].re, a[j].im);
-    else
-      mpole_f[(int64_t)(j - IP_PD) * ncells + c] = make_float2((float)a[j].re, (float)a[j].im);
-  }
+  for (int j = 0; j < IP_PD; ++j) mpole_d[(int64_t)j * ncells + c] = dfc_from_double(a[j].re, a[j].im);
+#pragma unroll
+  for (int j = 0; j < IP_P - IP_PD; ++j) mpole_f[(int64_t)j * ncells + c] = af[j];
 }
 
 // Translation kernels on the padded grid, scaled by n! / (Nx Ny):
