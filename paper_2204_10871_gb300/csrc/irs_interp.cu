@@ -12,10 +12,12 @@
 //             cells at Chebyshev distance 2..W: each lens directly (P2L);
 //             beyond W: multipole moments of each cell (P2M) translated to the
 //             target cell by a convolution over the regular cell grid (M2L),
-//             evaluated with FP64 FFTs;
+//             evaluated with FFTs, double-float for the low multipole and
+//             local orders and FP32 for the rest (IP_PD, IP_KD below);
 //             the rectangle sheet: its analytic part g(z), whose Taylor
 //             coefficients are closed-form (rational for order >= 2).
-//           All far-field accumulation is FP64.
+//           The per-cell sums (window lenses, sheet, first series terms)
+//           accumulate in FP64.
 //  level 2  each cell's series is re-centred on Q x Q sub-cells (the paper's
 //           level-2 grid points) with K2 terms, in shared memory per CTA.
 //  level 3  the rays: one CTA per cell; near lenses broadcast from shared
