@@ -900,7 +900,7 @@ def run_reference(args):
     qo = oracle.size(po)
     xy, m = lens_field(lensgen, (qo.a1, qo.a2, qo.b1, qo.b2), w["seed"])
     cores = os.cpu_count() or 1
-    budget = max(20.0, 60.0 / max(1, args.steps + args.warmup))
+    budget = max(0.1, args.ref_seconds)  # CPU seconds for the whole run (warm-up + timed)
     r0 = qo.nry // 2
     t0 = time.perf_counter()
     oracle.make_map(po, qo, xy, m, rows=(r0, r0 + cores), cols=(0, 32), threads=cores)
@@ -949,6 +949,8 @@ def main():
     ap.add_argument("--study", default="", choices=["", "accuracy", "planes", "border", "batched"],
                     help="one of the paper's side measurements instead of the benchmark (one GPU)")
     ap.add_argument("--ref-rays", type=float, default=4.0e10, help="rays of the accuracy study's reference map")
+    ap.add_argument("--ref-seconds", type=float, default=30.0,
+                    help="--impl reference: host CPU seconds for the oracle's warm-up and timed steps together")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps of the batched study")
     ap.add_argument("--shard", default="replicas", choices=["replicas", "strips"],
                     help="N > 1: a map per rank (weak scaling) or one map in row strips (strong)")
