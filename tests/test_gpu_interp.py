@@ -130,6 +130,37 @@ def test_c2_band_interp_vs_brute():
     assert rms <= REL_RMS_TOL, f"rel RMS {rms:.3e} over {npx} pixels"
 
 
+def test_c2_at_the_benchmark_configuration():
+    """The full mid-size workload in the launch configuration the benchmark
+    times: cell size and ray-pass variant picked by the autotuner on the same
+    lenses.  Sampled rays against the oracle, and the per-pixel magnification
+    of a band against the brute force."""
+    torch = require_gpu()
+    po, pl = params_pair(*C2, method=irs.IRS_INTERP, n_star=100000)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 100000, shape="salpeter", seed=2, kappa_star=C2[0])
+    dxy, dm = to_dev(torch, xy, m)
+    tuned, res = irs.irs_autotune(pl, dxy, dm)
+    assert res.candidates > 0 and res.ms_per_map > 0
+    err, far, pg, pixo, info = sampled_check(torch, C2, 100000, "salpeter", seed=2, nsamp=1500,
+                                             cell_mult=tuned.cell_mult, kernel_variant=tuned.kernel_variant)
+    assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
+    assert np.mean(pg != pixo) <= 2e-3
+    _, pl_b = params_pair(*C2, method=irs.IRS_BRUTE)
+    rows = (qo.nry // 2 - 256, qo.nry // 2 + 256)
+    maps = []
+    for p in (pl_b, tuned):
+        with irs.Plan(p) as plan:
+            c = torch.zeros((2000, 2000), dtype=torch.uint32, device="cuda")
+            irs.irs_make_map_rows(plan.handle, dxy, dm, rows[0], rows[1], c)
+            plan.sync()
+            maps.append(c.cpu().numpy())
+    cb, ci = maps
+    rms, npx = rel_rms(ci.astype(np.float64), cb.astype(np.float64), cb)
+    assert npx > 1000
+    assert rms <= REL_RMS_TOL, f"rel RMS {rms:.3e} over {npx} pixels"
+
+
 def test_interp_edge_cases():
     """No lenses; a lens count that is not a multiple of anything; circular
     plane (cell grid over the circle's bounding box); repeat determinism."""
