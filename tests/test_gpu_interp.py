@@ -47,6 +47,7 @@ def sampled_check(torch, cfg, n, shape, seed, nsamp=3000, kappa_rescale=True, pl
 
 C1 = (0.3, 0.0, 0.3, (-2.5, 2.5, -2.5, 2.5), 128, 25.0)
 C2 = (0.45, 0.0, 0.45, (-10.0, 10.0, -10.0, 10.0), 2000, 100.0)
+C3 = (0.35, 0.15, 0.4, (-12.5, 12.5, -12.5, 12.5), 10000, 40.0)
 
 
 def test_c1_sampled_deflection():
@@ -159,6 +160,25 @@ def test_c2_at_the_benchmark_configuration():
     rms, npx = rel_rms(ci.astype(np.float64), cb.astype(np.float64), cb)
     assert npx > 1000
     assert rms <= REL_RMS_TOL, f"rel RMS {rms:.3e} over {npx} pixels"
+
+
+def test_c3_full_size_sampled():
+    """The high-resolution workload at full size (1e6 lenses with masses
+    uniform in [0.1, 1], 10000^2 map, 9.6e10 rays), in the launch
+    configuration the autotuner picks on these lenses: sampled rays against
+    the oracle."""
+    torch = require_gpu()
+    po, pl = params_pair(*C3, method=irs.IRS_INTERP, n_star=1000000)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 1000000, shape="uniform", seed=3, kappa_star=C3[0])
+    dxy, dm = to_dev(torch, xy, m)
+    tuned, _ = irs.irs_autotune(pl, dxy, dm)
+    del dxy, dm
+    err, far, pg, pixo, info = sampled_check(torch, C3, 1000000, "uniform", seed=3, nsamp=800,
+                                             cell_mult=tuned.cell_mult, kernel_variant=tuned.kernel_variant)
+    assert info.n_rays > 9e10
+    assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
+    assert np.mean(pg != pixo) <= 2e-3
 
 
 def test_interp_edge_cases():
