@@ -3,14 +3,14 @@
 // (irs_df.cuh: 48-bit significands on the FP32 pipes; float4 elements) or in
 // FP32 (float2 elements).
 //
-// A CTA loads B lines of length L = 3^n3 2^n2 (144 KB of line buffer: 9216
-// double-float or 18432 FP32 complex values) into shared memory in mixed-radix
-// digit-reversed order, runs n3
-// radix-3 then n2 radix-2 in-place decimation-in-time stages with a twiddle
-// table W_L^t (t < L/2; W_L^(t + L/2) = -W_L^t) staged beside them, and writes
-// the lines back.  Rows are contiguous lines; columns are strided lines, loaded
-// B adjacent columns at a time so that each row segment is one coalesced
-// 16*B-byte access.  Zero padding is implicit: input elements at or beyond
+// A CTA loads B lines of length L = 3^n3 2^n2 into shared memory in
+// mixed-radix digit-reversed order (B as large as keeps the CTA within 52 KB,
+// so that up to four CTAs share an SM; at least one line, up to 9216
+// double-float or FP32 values), runs n3 radix-3 then n2 radix-2 in-place
+// decimation-in-time stages with a twiddle table W_L^t (t < L/2;
+// W_L^(t + L/2) = -W_L^t) staged beside them, and writes the lines back.
+// Rows are contiguous lines; columns are strided lines, loaded B adjacent
+// columns at a time so that each row segment is one coalesced access.  Zero padding is implicit: input elements at or beyond
 // `in_len` read as 0, and only the first `out_len` outputs of a line are
 // written.
 #include <math.h>

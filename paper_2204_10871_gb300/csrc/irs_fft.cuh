@@ -8,8 +8,8 @@
 
 namespace irs {
 
-constexpr int FFT_MAX_ELEMS = 9216;  // double-float complex values per CTA line buffer (144 KB;
-                                     // with the 72 KB twiddle table 216 KB of shared memory)
+constexpr int FFT_MAX_ELEMS = 9216;  // double-float complex values of the largest line buffer a CTA
+                                     // may hold (144 KB; with its 72 KB twiddle table 216 KB)
 constexpr int FFT_MAX_LEN = 9216;    // longest line (3^2 2^10)
 
 // One batched pass of 1-D FFTs over `n_lines` lines of length L.
