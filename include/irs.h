@@ -117,9 +117,14 @@ irs_status irs_plan_info_get(const irs_plan_t* plan, irs_plan_info* info);
  * write counts (npix_x*npix_y uint32, device, overwritten) and, when `mag` is
  * not NULL, Mag_ij = N_ij S_I / S_S (npix_x*npix_y float, device).  The
  * sheet's density is that of the lenses passed in, pi sum(m) / area.  n may
- * be 0.  Asynchronous on `stream`; may grow the workspace (synchronising) if
- * n exceeds the size the plan was made for.  Errors: IRS_ERR_ARG,
- * IRS_ERR_OOM, IRS_ERR_CUDA, IRS_ERR_NOT_TRAINED. */
+ * be 0.  Every lens must lie in the plan's lens region -- the rectangle that
+ * is both image and lens plane (Sec. 2.2), or the circumscribed circle for
+ * IRS_PLANE_CIRCLE -- to within 1e-9 of the plane's extent: the mass-sum pass
+ * checks every position on the device, and a lens outside (or a NaN position)
+ * makes the next irs_plan_sync return IRS_ERR_ARG.  Asynchronous on `stream`;
+ * may grow the workspace (synchronising) if n exceeds the size the plan was
+ * made for.  Errors: IRS_ERR_ARG, IRS_ERR_OOM, IRS_ERR_CUDA,
+ * IRS_ERR_NOT_TRAINED. */
 irs_status irs_make_map(irs_plan_t* plan, const double* lens_xy, const double* mass, int64_t n,
                         uint32_t* counts, float* mag, void* stream);
 
@@ -131,7 +136,9 @@ irs_status irs_make_map(irs_plan_t* plan, const double* lens_xy, const double* m
  * global counter.  The sequence is captured into a CUDA graph on the first call
  * with a given set of plans, pointers and lens counts, and later calls with the
  * same set replay the graph (the last 4 sets are kept; destroying a plan drops
- * the graphs that use it).  Arrays hold `nmaps` host-side entries; the pointers
+ * the graphs that use it).  A plan whose lens buffers were reallocated since
+ * (irs_make_map with more lenses than it had room for) is a new set: it is
+ * captured again, and no graph holding the old buffers is replayed.  Arrays hold `nmaps` host-side entries; the pointers
  * they hold are device pointers; `mag` (or any mag[k]) may be NULL.  Results
  * equal those of irs_make_map on each map.  Each plan may appear once (its
  * workspace serves one map).  The first call of a set allocates and
@@ -281,7 +288,12 @@ irs_status irs_mlp_forward(irs_plan_t* plan, const float* x, int64_t n, float* y
  * library holds until exit.  Limit: the ray lattice must fit 49,152 tiles of
  * 32 x 64 rays (about 1.0e8 rays); larger lattices return IRS_ERR_OVERFLOW
  * before any work is enqueued.  The first call on each device looks up the
- * array's device address (make it before any stream capture).  All calls share
+ * array's device address; where none of the library's device code has run on
+ * that device yet, it also loads that code (CUDA loads modules lazily by
+ * default), and the array is allocated then.  Make the first call on each
+ * device before any stream capture and outside latency-critical loops; later
+ * calls allocate nothing.  Lens positions are not checked against the lens
+ * region (there is no plan to report a device-side error to).  All calls share
  * the array: calls whose work overlaps on the GPU race.  Errors: IRS_ERR_ARG,
  * IRS_ERR_DEGENERATE, IRS_ERR_OVERFLOW, IRS_ERR_UNSUPPORTED (method other than
  * IRS_BRUTE), IRS_ERR_CUDA. */
@@ -290,7 +302,11 @@ irs_status irs_make_map_brute_noalloc(const irs_params* params, const double* le
                                       float* mag, void* stream);
 
 /* Wait for `stream` and return the first error a kernel of this plan raised
- * since the last sync (IRS_OK if none), clearing it. */
+ * since the last sync (IRS_OK if none), clearing it: IRS_ERR_ARG for a lens
+ * outside the plan's lens region, IRS_ERR_OVERFLOW when the 3 x 3 block of
+ * level-1 cells around some cell held more than the 1024 lenses the
+ * interpolated ray pass keeps in shared memory (that cell's near sum used the
+ * first 1024; the map is not valid).  The plan stays usable. */
 irs_status irs_plan_sync(irs_plan_t* plan, void* stream);
 
 /* Free the plan and its workspace (synchronises the device).  NULL is a no-op. */

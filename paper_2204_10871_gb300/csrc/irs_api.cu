@@ -144,7 +144,7 @@ irs_status run_map(irs_plan_t* P, const double* xy, const double* mass, int64_t 
   if (clear) IRS_TRY(cudaMemsetAsync(counts, 0, npix * sizeof(uint32_t), s));
   P->launches = 2;  // mass sum
   mark(P, irs::EV_START, s);
-  IRS_TRY(irs::launch_mass_sum(P, mass, n, s));
+  IRS_TRY(irs::launch_mass_sum(P, mass, n, s, xy));
   if (P->p.method == IRS_BRUTE) {
     IRS_TRY(irs::launch_brute_setup(P, s));
     mark(P, irs::EV_PREP, s);
@@ -309,7 +309,7 @@ irs_status irs_shoot_rays(irs_plan_t* P, const double* xy, const double* mass, i
   if (st != IRS_OK) return st;
   if (n_idx == 0) return IRS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  IRS_TRY(irs::launch_mass_sum(P, mass, n, s));
+  IRS_TRY(irs::launch_mass_sum(P, mass, n, s, xy));
   if (P->p.method == IRS_BRUTE) {
     IRS_TRY(irs::launch_brute_setup(P, s));
     IRS_TRY(irs::launch_brute_dump(P, xy, mass, n, ray_idx, n_idx, beta, pixel, s));

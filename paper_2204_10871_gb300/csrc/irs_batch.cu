@@ -18,6 +18,7 @@ namespace {
 
 constexpr int NSIDE = 8;       // capture streams the per-map stages are spread over
 constexpr int CACHE_SIZE = 4;  // graphs kept (least recently used dropped)
+constexpr size_t KEY_PER_MAP = 7;  // key words per map, after the device
 
 struct BatchEntry {
   std::vector<uintptr_t> key;
@@ -67,7 +68,7 @@ irs_status enqueue(BatchEntry* e, irs_plan_t* const* plans, int32_t nmaps, const
     cudaStream_t s = e->side[m % NSIDE];
     const size_t npix = (size_t)P->g.npix_x * P->g.npix_y;
     if (cudaMemsetAsync(counts[m], 0, npix * sizeof(uint32_t), s) != cudaSuccess) return IRS_ERR_CUDA;
-    if (irs::launch_mass_sum(P, mass[m], n[m], s) != cudaSuccess) return IRS_ERR_CUDA;
+    if (irs::launch_mass_sum(P, mass[m], n[m], s, xy[m]) != cudaSuccess) return IRS_ERR_CUDA;
     if (P->p.method == IRS_BRUTE) {
       if (irs::launch_brute_setup(P, s) != cudaSuccess) return IRS_ERR_CUDA;
       if (irs::launch_brute_map(P, xy[m], mass[m], n[m], 0, P->g.nry, counts[m], s) != cudaSuccess)
@@ -113,12 +114,8 @@ irs_status enqueue(BatchEntry* e, irs_plan_t* const* plans, int32_t nmaps, const
 irs_status build_entry(BatchEntry* e, irs_plan_t* const* plans, int32_t nmaps,
                        const double* const* xy, const double* const* mass, const int64_t* n,
                        uint32_t* const* counts, float* const* mag) {
-  // work that may allocate or synchronise happens before the capture
-  for (int32_t m = 0; m < nmaps; ++m)
-    if (plans[m]->p.method != IRS_BRUTE) {
-      irs_status st = irs::interp_ensure_capacity(plans[m], n[m]);
-      if (st != IRS_OK) return st;
-    }
+  // the lens buffers were grown by the caller, before the key was taken;
+  // streams, events and descriptors are made here, before the capture
   if (cudaGetDevice(&e->device) != cudaSuccess) return IRS_ERR_CUDA;
   if (cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking) != cudaSuccess) return IRS_ERR_CUDA;
   for (int k = 0; k < NSIDE; ++k)
@@ -187,6 +184,15 @@ extern "C" irs_status irs_make_maps_batched(irs_plan_t* const* plans, int32_t nm
     for (int32_t q = 0; q < m; ++q)  // stages of one map run concurrently with the others':
       if (plans[q] == plans[m]) return IRS_ERR_ARG;  // a plan's workspace serves one map
   }
+  std::lock_guard<std::mutex> lock(g_mu);
+  // lens buffers grow (and move) before the key is taken: a graph is keyed by
+  // every address its kernels use, the plans' workspace generations included,
+  // so a graph captured before a plan's buffers moved is never replayed
+  for (int32_t m = 0; m < nmaps; ++m)
+    if (plans[m]->p.method != IRS_BRUTE) {
+      irs_status st = irs::interp_ensure_capacity(plans[m], n[m]);
+      if (st != IRS_OK) return st;
+    }
   std::vector<uintptr_t> key;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IRS_ERR_CUDA;
@@ -198,8 +204,8 @@ extern "C" irs_status irs_make_maps_batched(irs_plan_t* const* plans, int32_t nm
     key.push_back((uintptr_t)n[m]);
     key.push_back((uintptr_t)counts[m]);
     key.push_back((uintptr_t)(mag ? mag[m] : nullptr));
+    key.push_back((uintptr_t)plans[m]->ws_gen);
   }
-  std::lock_guard<std::mutex> lock(g_mu);
   BatchEntry* e = nullptr;
   for (BatchEntry* c : g_cache)
     if (c->key == key) e = c;
@@ -230,7 +236,7 @@ void irs_batch_forget_plan(const irs_plan_t* plan) {
   std::lock_guard<std::mutex> lock(g_mu);
   for (size_t k = 0; k < g_cache.size();) {
     bool hit = false;
-    for (size_t i = 1; i < g_cache[k]->key.size(); i += 6)
+    for (size_t i = 1; i < g_cache[k]->key.size(); i += KEY_PER_MAP)
       if (g_cache[k]->key[i] == (uintptr_t)plan) hit = true;
     if (hit) {
       release(g_cache[k]);

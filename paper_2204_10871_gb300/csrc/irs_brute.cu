@@ -22,13 +22,38 @@ namespace irs {
 
 // ------------------------------------------------------------ mass sum (FP64)
 // Deterministic two-pass sum of the masses: fixed strides per thread, fixed
-// reduction tree, fixed order of the block partials.
-__global__ void k_mass_partial(const double* __restrict__ mass, int64_t n,
-                               double* __restrict__ part) {
+// reduction tree, fixed order of the block partials.  With lens positions
+// given, the same pass checks that every lens lies in the plan's lens region
+// (the rectangle that is both image and lens plane, Sec. 2.2, or the
+// circumscribed circle), with a margin of 1e-9 of the plane's extent for
+// positions drawn on its edges: a lens outside it (or a NaN position) sets
+// IRS_ERR_ARG in the plan's status word unless an earlier error is there.
+struct LensRegion {
+  double x0, x1, y0, y1;  // rectangle, margin included
+  double cx, cy, r2;      // circle: centre and squared radius, margin included
+  int32_t circle;
+  int32_t check;          // 0: positions not given, no check
+};
+
+__device__ __forceinline__ bool lens_inside(const LensRegion& L, double2 p) {
+  if (L.circle) {
+    const double dx = p.x - L.cx, dy = p.y - L.cy;
+    return dx * dx + dy * dy <= L.r2;  // false for NaN
+  }
+  return p.x >= L.x0 && p.x <= L.x1 && p.y >= L.y0 && p.y <= L.y1;
+}
+
+__global__ void k_mass_partial(const double* __restrict__ mass, const double2* __restrict__ xy, int64_t n,
+                               LensRegion region, int* __restrict__ status, double* __restrict__ part) {
   __shared__ double sh[MSUM_THREADS];
   double s = 0.0;
+  bool outside = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) s += mass[k];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    s += mass[k];
+    if (region.check) outside |= !lens_inside(region, xy[k]);
+  }
+  if (__syncthreads_or(outside) && threadIdx.x == 0) atomicCAS(status, 0, (int)IRS_ERR_ARG);
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int w = MSUM_THREADS / 2; w > 0; w >>= 1) {
@@ -46,8 +71,24 @@ __global__ void k_mass_final(const double* __restrict__ part, double* __restrict
   }
 }
 
-cudaError_t launch_mass_sum(const irs_plan_t* P, const double* mass, int64_t n, cudaStream_t s) {
-  k_mass_partial<<<MSUM_BLOCKS, MSUM_THREADS, 0, s>>>(mass, n, P->d_mpart);
+cudaError_t launch_mass_sum(const irs_plan_t* P, const double* mass, int64_t n, cudaStream_t s,
+                            const double* xy) {
+  LensRegion L{};
+  const Geo& g = P->g;
+  const double ext = fmax(fmax(fabs(g.a1), fabs(g.a2)), fmax(fmax(fabs(g.b1), fabs(g.b2)),
+                                                             fmax(g.a2 - g.a1, g.b2 - g.b1)));
+  const double tol = 1e-9 * ext;
+  L.x0 = g.a1 - tol;
+  L.x1 = g.a2 + tol;
+  L.y0 = g.b1 - tol;
+  L.y1 = g.b2 + tol;
+  L.cx = g.cx;
+  L.cy = g.cy;
+  L.r2 = (P->circle_r + tol) * (P->circle_r + tol);
+  L.circle = g.plane == IRS_PLANE_CIRCLE;
+  L.check = xy != nullptr && n > 0;
+  k_mass_partial<<<MSUM_BLOCKS, MSUM_THREADS, 0, s>>>(mass, reinterpret_cast<const double2*>(xy), n, L,
+                                                      P->d_status, P->d_mpart);
   k_mass_final<<<1, 32, 0, s>>>(P->d_mpart, P->d_msum);
   return cudaGetLastError();
 }

@@ -175,6 +175,9 @@ struct irs_plan {
   int num_sms;
   // INTERP state (irs_interp.cu)
   void* interp;
+  // bumped whenever a device buffer that kernels address is reallocated, so
+  // that captured graphs holding the old addresses are never replayed
+  uint64_t ws_gen;
   // learned far field state (irs_mlp.cu), IRS_MLP plans only
   void* mlp;
   // stage timing (irs_plan_set_timing)
@@ -190,7 +193,11 @@ constexpr int MSUM_BLOCKS = 128;
 constexpr int MSUM_THREADS = 256;
 
 // launchers implemented in irs_brute.cu
-cudaError_t launch_mass_sum(const irs_plan_t* P, const double* mass, int64_t n, cudaStream_t s);
+// Sum of the masses into d_msum; with lens positions `xy` given (2n doubles),
+// also the check that every lens lies in the plan's lens region (IRS_ERR_ARG
+// into d_status otherwise).
+cudaError_t launch_mass_sum(const irs_plan_t* P, const double* mass, int64_t n, cudaStream_t s,
+                            const double* xy = nullptr);
 cudaError_t launch_brute_setup(const irs_plan_t* P, cudaStream_t s);
 cudaError_t launch_brute_map(const irs_plan_t* P, const double* xy, const double* mass, int64_t n,
                              int64_t row0, int64_t row1, uint32_t* counts, cudaStream_t s);

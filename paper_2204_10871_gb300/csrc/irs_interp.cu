@@ -747,7 +747,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     if (lane == 8) {
       int off = inc;
       if (off > IP_NEAR_MAX) {
-        atomicExch(a.status, (int)IRS_ERR_OVERFLOW);
+        atomicCAS(a.status, 0, (int)IRS_ERR_OVERFLOW);  // the first error stays
         off = IP_NEAR_MAX;
       }
       blk_off[9] = off;
@@ -1137,7 +1137,8 @@ cudaError_t launch_ip_ray_batch(int variant, int64_t grid, cudaStream_t s, const
 }
 
 // ------------------------------------------------------------ host helpers
-irs_status alloc_lens_buffers(InterpState* S, int64_t cap) {
+irs_status alloc_lens_buffers(irs_plan_t* P, InterpState* S, int64_t cap) {
+  ++P->ws_gen;  // the lens buffers move: graphs captured on the old ones are stale
   if (S->lens_ws) cudaFree(S->lens_ws);
   S->lens_ws = nullptr;
   cap = cap < 256 ? 256 : cap;
@@ -1189,7 +1190,7 @@ irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* ma
   const int64_t ncells = (int64_t)ig.ncx * ig.ncy;
   if (n > S->cap) {
     cudaStreamSynchronize(s);
-    irs_status st = alloc_lens_buffers(S, n + n / 4);
+    irs_status st = alloc_lens_buffers(P, S, n + n / 4);
     if (st != IRS_OK) return st;
   }
   const double2* xy2 = reinterpret_cast<const double2*>(xy);
@@ -1355,7 +1356,7 @@ irs_status interp_plan(irs_plan_t* P) {
   S->kspec_f = reinterpret_cast<float2*>(b + o_ksf);
   S->recs = reinterpret_cast<CellRec*>(b + o_rec);
   S->coef = reinterpret_cast<float2*>(b + o_coef);
-  irs_status st = alloc_lens_buffers(S, nstar + nstar / 4 + 256);
+  irs_status st = alloc_lens_buffers(P, S, nstar + nstar / 4 + 256);
   if (st != IRS_OK) return st;
   // translation kernels and their spectra, once per plan
   const int nker = ig.P + IP_KF - 1;
@@ -1439,7 +1440,7 @@ irs_status interp_ensure_capacity(irs_plan_t* P, int64_t n) {
   InterpState* S = S_(P);
   if (n <= S->cap) return IRS_OK;
   if (cudaDeviceSynchronize() != cudaSuccess) return IRS_ERR_CUDA;
-  return alloc_lens_buffers(S, n + n / 4);
+  return alloc_lens_buffers(P, S, n + n / 4);
 }
 
 irs_status interp_prepare(irs_plan_t* P, const double* xy, const double* mass, int64_t n,

@@ -10,10 +10,14 @@
 // setup records) in one file-scope __device__ array, so it allocates nothing.
 // Inputs and outputs are still the caller's buffers.
 //
-// The array is part of the library image: every GPU that loads the library
-// holds its 7.9 MB until the process exits.  Its device address is looked up
-// with cudaGetSymbolAddress on the first call made on each device (with that
-// device current); make that first call before any stream capture.  All calls
+// The array is part of the library image: every GPU that loads the library's
+// device code holds its 7.9 MB until the process exits.  CUDA loads device
+// code lazily by default, so on a device where nothing of the library has run
+// yet, the first call loads it and the array is allocated then, by the
+// driver.  Its device address is looked up with cudaGetSymbolAddress on the
+// first call made on each device (with that device current).  Make that
+// first call before any stream capture and outside latency-critical loops;
+// later calls allocate nothing.  All calls
 // share the one array and it keeps the last call's contents, so calls whose
 // work overlaps on the GPU (different streams, or different host threads
 // without ordering) race on it.
@@ -78,7 +82,10 @@ extern "C" irs_status irs_make_map_brute_noalloc(const irs_params* params, const
   if (p.npix_x <= 0 || p.npix_y <= 0 || !(p.rays_per_pixel > 0)) return IRS_ERR_ARG;
   if ((int64_t)p.npix_x * p.npix_y >= ((int64_t)1 << 32) - 1) return IRS_ERR_OVERFLOW;
   if (!(p.src_x1 > p.src_x0) || !(p.src_y1 > p.src_y0)) return IRS_ERR_ARG;
-  if (p.kappa_star < 0 || p.kappa_s < 0 || p.flags != 0) return IRS_ERR_ARG;
+  if (p.kappa_star < 0 || p.kappa_s < 0 || p.n_star < 0 || p.flags != 0) return IRS_ERR_ARG;
+  for (int k = 0; k < 6; ++k)  // the parameter checks of irs_plan
+    if (p.reserved[k] != 0) return IRS_ERR_ARG;
+  if (!isfinite(p.cell_mult) || p.cell_mult < 0 || p.far_order < 0 || p.window < 0) return IRS_ERR_ARG;
   if (p.plane != IRS_PLANE_RECT && p.plane != IRS_PLANE_CIRCLE) return IRS_ERR_ARG;
   if (p.method != IRS_BRUTE) return IRS_ERR_UNSUPPORTED;
   if (p.kernel_variant != 0) return IRS_ERR_UNSUPPORTED;  // the default brute kernel only

@@ -1,5 +1,7 @@
 """Helpers shared by the GPU parity tests: build/load the CUDA library, the
 seeded workloads, and comparisons against the FP64 oracle."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -79,3 +81,29 @@ def ray_positions(plan_o, idx):
     i = idx % plan_o.nrx
     j = idx // plan_o.nrx
     return np.stack([plan_o.a1 + (i + 0.5) * plan_o.dx3, plan_o.b1 + (j + 0.5) * plan_o.dx3], 1)
+
+
+# The mid-size workload (kappa_* = gamma = 0.45, 1e5 Salpeter lenses, 2000^2
+# map over 20 x 20 theta_E, 100 rays per unlensed pixel) and a band of whole
+# lattice rows across its middle that the oracle shoots in ~20 s on 16 cores
+# (3 rows of 334,166 rays, every lens).
+C2 = (0.45, 0.0, 0.45, (-10.0, 10.0, -10.0, 10.0), 2000, 100.0)
+C2_N = 100000
+C2_ROWS = 3
+
+
+def c2_lenses(plan_o):
+    return lenses_for(plan_o, C2_N, shape="salpeter", seed=2, kappa_star=C2[0])
+
+
+@functools.lru_cache(maxsize=1)
+def c2_oracle_rows():
+    """(rows, oracle counts, landed) of the full-width band, computed once per
+    test session."""
+    po = oracle.make_params(*C2)
+    qo = oracle.size(po)
+    xy, m = c2_lenses(qo)
+    r0 = qo.nry // 2
+    rows = (r0, r0 + C2_ROWS)
+    co, _, landed = oracle.make_map(po, qo, xy, m, rows=rows)
+    return rows, co, landed

@@ -10,8 +10,9 @@ import pytest
 
 import oracle
 from paper_2204_10871_gb300 import irs
-from gpu_common import (DEFLECTION_TOL, MISBIN_TOL, NEAR_LENS, lenses_for, misbinned,
-                        nearest_lens_distance, params_pair, ray_positions, require_gpu, to_dev)
+from gpu_common import (C2, DEFLECTION_TOL, MISBIN_TOL, NEAR_LENS, c2_lenses, c2_oracle_rows, lenses_for,
+                        misbinned, nearest_lens_distance, params_pair, ray_positions, require_gpu,
+                        to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -141,6 +142,52 @@ def test_circle_plane_point_lens():
                          plane=irs.IRS_PLANE_CIRCLE)
     qo, co, mo, landed, cg, mg = _map_pair(torch, po, pl, np.zeros((1, 2)), np.ones(1))
     assert misbinned(co, cg) <= MISBIN_TOL * landed
+
+
+@pytest.mark.parametrize("src", [(1.0, 3.0, -2.5, -0.5), (-9.0, -5.0, 2.0, 6.5)])
+def test_circle_plane_off_centre(src):
+    """Eq. (alpha) for a circular plane centred away from the origin (the
+    k_* theta_c term of the circle sheet is non-zero): map and sampled
+    deflections against the oracle."""
+    torch = require_gpu()
+    po, pl = params_pair(0.3, 0.05, 0.25, src, 96, 16.3, plane=irs.IRS_PLANE_CIRCLE)
+    qo = oracle.size(po)
+    assert np.hypot(qo.cx, qo.cy) > 2.0
+    xy, m = lenses_for(qo, 200, shape="uniform", seed=17, kappa_star=0.3, plane=irs.IRS_PLANE_CIRCLE)
+    qo, co, mo, landed, cg, mg = _map_pair(torch, po, pl, xy, m)
+    bad = misbinned(co, cg)
+    assert bad <= MISBIN_TOL * landed, f"{bad} of {landed} rays binned differently"
+    idx = np.random.default_rng(6).integers(0, qo.n_rays, 3000).astype(np.int64)
+    _, bo, _ = oracle.shoot_rays(po, qo, xy, m, idx)
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        beta, _ = plan.shoot_rays(dxy, dm, torch.from_numpy(idx).cuda())
+        plan.sync()
+    err = np.abs(beta.cpu().numpy() - bo).max(1)
+    far = nearest_lens_distance(xy, ray_positions(qo, idx)) > NEAR_LENS
+    assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
+
+
+def test_c2_full_width_rows_vs_oracle():
+    """The full mid-size workload (1e5 lenses, 2000^2 map, 100 rays/px): three
+    whole lattice rows across the middle of the plane (1.0e6 rays, every ray
+    summed over every lens by the oracle in FP64) against the same rows of the
+    GPU brute force, at the misbinning bar."""
+    torch = require_gpu()
+    rows, co, landed = c2_oracle_rows()
+    po, pl = params_pair(*C2, method=irs.IRS_BRUTE)
+    qo = oracle.size(po)
+    xy, m = c2_lenses(qo)
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        c = torch.zeros((2000, 2000), dtype=torch.uint32, device="cuda")
+        irs.irs_make_map_rows(plan.handle, dxy, dm, rows[0], rows[1], c)
+        plan.sync()
+    cg = c.cpu().numpy()
+    bad = misbinned(co, cg)
+    print(f"\nbrute, rows {rows}: {bad} of {landed} rays binned differently ({bad / landed:.2e})")
+    assert landed > 500000
+    assert bad <= MISBIN_TOL * landed, f"{bad} of {landed} rays binned differently"
 
 
 def test_repeat_is_deterministic():

@@ -11,8 +11,9 @@ import pytest
 
 import oracle
 from paper_2204_10871_gb300 import irs
-from gpu_common import (DEFLECTION_TOL, MISBIN_TOL, NEAR_LENS, lenses_for, misbinned,
-                        nearest_lens_distance, params_pair, ray_positions, require_gpu, to_dev)
+from gpu_common import (DEFLECTION_TOL, MISBIN_TOL, NEAR_LENS, c2_lenses, c2_oracle_rows, lenses_for,
+                        misbinned, nearest_lens_distance, params_pair, ray_positions, require_gpu,
+                        to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -84,6 +85,54 @@ def test_dense_fields_sampled(cfg, n, shape):
     err, far, pg, pixo, info = sampled_check(torch, cfg, n, shape, seed=9)
     assert info.ncell_x >= 8 or info.ncell_y >= 8
     assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
+
+
+@pytest.mark.parametrize("src", [(1.0, 3.0, -2.5, -0.5), (-9.0, -5.0, 2.0, 6.5)])
+def test_circle_plane_off_centre(src):
+    """A circular plane centred away from the origin (cell grid over the
+    circle's bounding box, the k_* theta_c term non-zero): sampled deflections
+    and the map against the oracle."""
+    torch = require_gpu()
+    cfg = (0.3, 0.05, 0.25, src, 96, 16.3)
+    err, far, pg, pixo, info = sampled_check(torch, cfg, 200, "uniform", seed=17,
+                                             plane=irs.IRS_PLANE_CIRCLE)
+    assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
+    po, pl = params_pair(*cfg, plane=irs.IRS_PLANE_CIRCLE, method=irs.IRS_INTERP, n_star=200)
+    qo = oracle.size(po)
+    xy, m = lenses_for(qo, 200, shape="uniform", seed=17, kappa_star=0.3, plane=irs.IRS_PLANE_CIRCLE)
+    co, _, landed = oracle.make_map(po, qo, xy, m)
+    with irs.Plan(pl) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        counts, _ = plan.make_map(dxy, dm, with_mag=False)
+        plan.sync()
+    bad = misbinned(co, counts.cpu().numpy())
+    assert bad <= MISBIN_TOL * landed, f"{bad} of {landed} rays binned differently"
+
+
+def _c2_rows_misbinned(torch, params):
+    """Rays binned differently from the oracle on the full-width band of the
+    mid-size workload, for an interpolated plan made from `params`."""
+    rows, co, landed = c2_oracle_rows()
+    po = oracle.make_params(*C2)
+    qo = oracle.size(po)
+    xy, m = c2_lenses(qo)
+    with irs.Plan(params) as plan:
+        dxy, dm = to_dev(torch, xy, m)
+        c = torch.zeros((2000, 2000), dtype=torch.uint32, device="cuda")
+        irs.irs_make_map_rows(plan.handle, dxy, dm, rows[0], rows[1], c)
+        plan.sync()
+    return misbinned(co, c.cpu().numpy()), landed
+
+
+def test_c2_full_width_rows_vs_oracle():
+    """Three whole lattice rows across the full mid-size workload (1.0e6 rays,
+    1e5 lenses), the paper-rule cells: the interpolated map of these rays
+    against the oracle's brute force, at the brute force's misbinning bar."""
+    torch = require_gpu()
+    _, pl = params_pair(*C2, method=irs.IRS_INTERP, n_star=100000)
+    bad, landed = _c2_rows_misbinned(torch, pl)
+    print(f"\ninterp (rule cells): {bad} of {landed} rays binned differently ({bad / landed:.2e})")
+    assert bad <= MISBIN_TOL * landed, f"{bad} of {landed} rays binned differently"
 
 
 def test_c2_full_size_sampled():
@@ -160,6 +209,10 @@ def test_c2_at_the_benchmark_configuration():
     rms, npx = rel_rms(ci.astype(np.float64), cb.astype(np.float64), cb)
     assert npx > 1000
     assert rms <= REL_RMS_TOL, f"rel RMS {rms:.3e} over {npx} pixels"
+    bad, landed = _c2_rows_misbinned(torch, tuned)
+    print(f"\ninterp (tuned: cell_mult {tuned.cell_mult:.4f}, variant {tuned.kernel_variant}): "
+          f"{bad} of {landed} rays binned differently from the oracle ({bad / landed:.2e})")
+    assert bad <= MISBIN_TOL * landed, f"{bad} of {landed} rays binned differently"
 
 
 def test_c3_full_size_sampled():

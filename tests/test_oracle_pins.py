@@ -127,6 +127,94 @@ def test_deflection_circle_plane_matches_eq_alpha():
     assert np.allclose(oracle.deflection(p, q, xy, m, *t), ref, rtol=0, atol=1e-14)
 
 
+def _disc_sheet_quadrature(cx, cy, R, k, t1, t2, npts=4096):
+    """Deflection of a POSITIVE uniform disc of density k, radius R, centre
+    (cx, cy), at a point inside it, by an independent route: in polar
+    coordinates about the field point the 2-D integral
+    (k/pi) int (theta - theta') / |theta - theta'|^2 d^2 theta' reduces to
+    -(k/pi) int_0^2pi rho(phi) u(phi) dphi, with u = (cos phi, sin phi) and
+    rho(phi) the distance to the disc's edge along u; the integrand is smooth
+    and periodic, so the trapezoid rule converges geometrically."""
+    phi = np.arange(npts) * (2.0 * np.pi / npts)
+    ux, uy = np.cos(phi), np.sin(phi)
+    px, py = t1 - cx, t2 - cy
+    pu = px * ux + py * uy
+    rho = -pu + np.sqrt(pu * pu - (px * px + py * py) + R * R)
+    w = 2.0 * np.pi / npts
+    return (-(k / np.pi) * w * np.sum(rho * ux), -(k / np.pi) * w * np.sum(rho * uy))
+
+
+def test_disc_quadrature_route_is_newtons_theorem():
+    """The quadrature helper itself: a centred point sees no pull, and inside
+    an off-centre disc the pull is k (theta - theta_c) (Newton's theorem, the
+    circle limit of Eq. (alphapart) with the sign of a positive sheet)."""
+    assert np.allclose(_disc_sheet_quadrature(1.0, -2.0, 3.0, 0.4, 1.0, -2.0), (0.0, 0.0), atol=1e-14)
+    for t in [(2.5, -1.0), (-1.2, -3.9), (1.0, 0.9)]:
+        o = _disc_sheet_quadrature(1.0, -2.0, 3.0, 0.4, *t)
+        assert np.allclose(o, (0.4 * (t[0] - 1.0), 0.4 * (t[1] + 2.0)), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("src", [(1.0, 3.0, -2.5, -0.5), (-7.0, -3.0, 4.0, 9.0)])
+def test_off_centre_circle_plane_is_eq_alpha1_with_the_disc_sheet(src):
+    """Eq. (alpha1) with the circular negative sheet of a plane NOT centred on
+    the origin: the matrix term diag(k + g, k - g) theta with k = k_s + k_*
+    (k_* of the lenses passed in), the lens sum, and minus the disc's own pull
+    computed by quadrature (not by the oracle's k_* theta_c closed form).
+    Catches a dropped or sign-flipped k_* theta_c term of the oracle's circle
+    branch, or a disc centred on the origin instead of the plane centre."""
+    p = oracle.make_params(0.3, 0.1, 0.2, src, 16, 4.0, plane=oracle.PLANE_CIRCLE)
+    q = oracle.size(p)
+    assert np.hypot(q.cx, q.cy) > 2.0  # theta_c far from the origin
+    xy, m = lensgen.lens_field(60, None, shape="uniform", seed=13, disc=(q.cx, q.cy, q.circle_r))
+    ks = m.sum() / q.circle_r ** 2  # pi sum(m) / (pi R^2)
+    kap = p.kappa_s + ks
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        t = np.array([rng.uniform(q.a1, q.a2), rng.uniform(q.b1, q.b2)])
+        d = t - xy
+        lens = (m[:, None] * d / (d * d).sum(1)[:, None]).sum(0)
+        disc = np.array(_disc_sheet_quadrature(q.cx, q.cy, q.circle_r, ks, *t))
+        ref = np.array([(kap + p.gamma) * t[0], (kap - p.gamma) * t[1]]) + lens - disc
+        assert np.allclose(oracle.deflection(p, q, xy, m, *t), ref, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("plane", [oracle.PLANE_RECT, oracle.PLANE_CIRCLE])
+def test_translation_covariance_of_the_lens_equation(plane):
+    """Moving the source region by d_beta moves the plane centre by
+    theta_c = (d_beta_1 / (1 - k - g), d_beta_2 / (1 - k + g)); with every lens
+    moved by theta_c too, each lattice ray must land exactly d_beta away
+    (beta' - beta = diag(1 - k - g, 1 - k + g) theta_c with the sheet moving
+    with the plane), so the two maps agree pixel for pixel.  A missing or
+    sign-flipped k_* theta_c term (circle) or a sheet that does not follow the
+    plane (rectangle) shifts every ray by k_* theta_c instead."""
+    base = (-2.5, 2.5, -2.5, 2.5)
+    dbeta = (3.25, -1.75)
+    moved = (base[0] + dbeta[0], base[1] + dbeta[0], base[2] + dbeta[1], base[3] + dbeta[1])
+    args = (0.3, 0.05, 0.25)
+    p0 = oracle.make_params(*args, base, 24, 9.3, plane=plane)
+    p1 = oracle.make_params(*args, moved, 24, 9.3, plane=plane)
+    q0, q1 = oracle.size(p0), oracle.size(p1)
+    assert (q0.nrx, q0.nry) == (q1.nrx, q1.nry)
+    tc = np.array([q1.cx - q0.cx, q1.cy - q0.cy])
+    lam = np.array([1.0 - q0.kappa - p0.gamma, 1.0 - q0.kappa + p0.gamma])
+    assert np.allclose(lam * tc, dbeta, rtol=1e-14, atol=1e-14)
+    if plane == oracle.PLANE_CIRCLE:
+        xy0, m = lensgen.lens_field(80, None, shape="uniform", seed=21, disc=(q0.cx, q0.cy, q0.circle_r))
+    else:
+        xy0, m = lensgen.lens_field(80, (q0.a1, q0.a2, q0.b1, q0.b2), shape="uniform", seed=21)
+    m = m * (0.3 / oracle.kappa_star_actual(p0, q0, m))  # kappa_* = 0.3 exactly
+    xy1 = xy0 + tc
+    idx = np.random.default_rng(4).integers(0, q0.n_rays, 400)
+    _, b0, _ = oracle.shoot_rays(p0, q0, xy0, m, idx)
+    _, b1, _ = oracle.shoot_rays(p1, q1, xy1, m, idx)
+    assert np.allclose(b1 - b0, dbeta, rtol=0, atol=1e-9)
+    c0, _, n0 = oracle.make_map(p0, q0, xy0, m)
+    c1, _, n1 = oracle.make_map(p1, q1, xy1, m)
+    # rays within rounding of a pixel edge may go either way
+    assert np.abs(c0.astype(np.int64) - c1.astype(np.int64)).sum() <= 4
+    assert abs(n0 - n1) <= 2 and n0 > 1000
+
+
 def test_tiny_field_against_quadrature_route():
     """Brute force on a tiny input by an independent route: numpy lens sum plus
     the rectangle sheet by 2-D quadrature (not the closed form)."""
