@@ -19,6 +19,14 @@ rays / the slowest rank's time.  --shard strips makes ONE map over all ranks
 (strong scaling): each rank shoots a strip of whole cell rows and the count
 maps are summed (one all-reduce per map, inside the timed step).
 
+The default run (one GPU, paper-mid interp) adds three sub-records to its
+line, measured after the timed steps: "high_res" (the 1e6-lens, 10000^2,
+9.6e10-ray workload: whole-map rays/s, ray-pass roofline, error and speed-up
+against a brute-force band), "learned" (the learned far field's workload:
+learned and series forms against a brute-force band) and "batched" (256
+uneven maps in one captured graph against one call per map).  --no-extra
+skips them.
+
 --study accuracy | planes | border replays the paper's accuracy-vs-rays slope,
 its rectangular vs circular lens plane comparison and its protective-border
 deflection distribution (one GPU; one JSON line each).
@@ -386,6 +394,17 @@ def run_ours(args):
             learned["interp_map_rel_rms_vs_brute"] = band_rel_rms(irs, torch, pi, dxy, dm, band, shape)
         pi.close()
 
+    # ---- the other workloads of the hot path, one GPU: high resolution, the
+    # batched persistent launch, the learned far field (sub-records)
+    extra = {}
+    if world == 1 and args.method == "interp" and not args.no_extra and not (args.n_star or args.npix or args.nav):
+        extra["high_res"] = high_res_record(irs, torch, lensgen, n_sms, peak_tflops, flush)
+        torch.cuda.empty_cache()
+        extra["learned"] = learned_record(irs, torch, lensgen, flush)
+        torch.cuda.empty_cache()
+        extra["batched"] = batched_measure(torch, irs, lensgen, 256, 1, 3)
+        torch.cuda.empty_cache()
+
     if rank == 0:
         cpu = cpu_baseline(xy, m, w) if (world == 1 and not args.no_cpu) else None
         line = {
@@ -406,7 +425,9 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "autotune": tune,
-            "learned": learned,
+            "learned": learned if learned is not None else extra.get("learned"),
+            "high_res": extra.get("high_res"),
+            "batched": extra.get("batched"),
             "roofline": roofline,
             "clocks": clocks,
             "stage_ms": {"raypass_mean": ray_ms_mean, "map_total_mean": float(np.mean(tot_ms)),
@@ -473,6 +494,134 @@ def brute_band(irs, torch, w, xy, m, dxy, dm, band, plan_fast, n_sms, peak_tflop
             "speedup_of_fast_method": fast_value / value,
             "map_rel_rms_vs_brute": float(np.sqrt(np.mean(rel * rel))) if sel.any() else None,
             "pixels_compared": int(sel.sum()), "min_rays_per_pixel": 100}
+
+
+def timed_maps(irs, torch, plan, dxy, dm, counts, mag, flush, reps=3):
+    """Mean CUDA-event time (ms) of a whole map and of its ray pass over `reps`
+    maps after one warm-up map, with L2 flushed before each."""
+    irs.irs_plan_set_timing(plan.handle, True)
+    irs.irs_make_map(plan.handle, dxy, dm, counts, mag)
+    plan.sync()
+    tot, ray = [], []
+    for k in range(reps):
+        flush.fill_(float(k))
+        irs.irs_make_map(plan.handle, dxy, dm, counts, mag)
+        t = irs.irs_plan_timings(plan.handle)
+        tot.append(t.ms_total)
+        ray.append(t.ms_raypass)
+    plan.sync()
+    return float(np.mean(tot)), float(np.mean(ray))
+
+
+def band_pair(irs, torch, w, dxy, dm, band, plans_fast):
+    """The brute force over lattice rows `band` (timed once, CUDA events) and
+    the same rows made by each plan of `plans_fast`: brute rays/s and each
+    fast map's per-pixel magnification rel RMS against the brute force over
+    pixels with >= 100 rays."""
+    shape = (w["npix"], w["npix"])
+    pb = irs.Plan(workload_params(irs, "brute", w))
+    irs.irs_plan_set_timing(pb.handle, True)
+    cb = torch.zeros(shape, dtype=torch.uint32, device=dxy.device)
+    irs.irs_make_map_rows(pb.handle, dxy, dm, band[0], band[1], cb)
+    t = irs.irs_plan_timings(pb.handle)
+    pb.sync()
+    rays = (band[1] - band[0]) * pb.info.n_rays_x
+    pb.close()
+    a = cb.cpu().numpy().astype(np.float64)
+    del cb
+    sel = a >= 100
+    rels = []
+    for pf in plans_fast:
+        c = torch.zeros(shape, dtype=torch.uint32, device=dxy.device)
+        irs.irs_make_map_rows(pf.handle, dxy, dm, band[0], band[1], c)
+        pf.sync()
+        b = c.cpu().numpy().astype(np.float64)
+        del c
+        r = (b[sel] - a[sel]) / a[sel]
+        rels.append(float(np.sqrt(np.mean(r * r))) if sel.any() else None)
+    return {"rays_per_s": rays / (t.ms_total * 1e-3), "band_rows": [int(band[0]), int(band[1])],
+            "rays": int(rays), "ms": float(t.ms_total), "ms_raypass": float(t.ms_raypass),
+            "pixels_compared": int(sel.sum())}, rels
+
+
+def high_res_record(irs, torch, lensgen, n_sms, peak_tflops, flush):
+    """The high-resolution workload (1e6 lenses, 10000^2 map, 40 rays/px,
+    9.6e10 rays; the 400 MB count map is larger than L2), autotuned: whole-map
+    rays/s, the ray pass's FP32 roofline, and the per-pixel magnification rel
+    RMS against the brute force on a 64-row band (one brute-force tile row)."""
+    w = WORKLOAD_HIGHRES
+    dev = torch.device("cuda", torch.cuda.current_device())
+    params = workload_params(irs, "interp", w)
+    with irs.Plan(params) as probe:
+        box = (probe.info.lens_x0, probe.info.lens_x1, probe.info.lens_y0, probe.info.lens_y1)
+    xy, m = lens_field(lensgen, box, w["seed"], w)
+    dxy, dm = torch.from_numpy(xy).to(dev), torch.from_numpy(m).to(dev)
+    t0 = time.perf_counter()
+    params, res = irs.irs_autotune(params, dxy, dm)
+    tune_s = time.perf_counter() - t0
+    plan = irs.Plan(params)
+    info = plan.info
+    shape = (w["npix"], w["npix"])
+    counts = torch.zeros(shape, dtype=torch.uint32, device=dev)
+    mag = torch.zeros(shape, dtype=torch.float32, device=dev)
+    ms_map, ms_ray = timed_maps(irs, torch, plan, dxy, dm, counts, mag, flush)
+    del counts, mag
+    variant = int(params.kernel_variant)
+    n_near = mean_near_lenses(info, xy)
+    flops = 10.0 * n_near + ip_flops_fixed(variant)
+    ach = flops * info.n_rays / (ms_ray * 1e-3) / 1e12
+    r0 = (info.n_rays_y // 2 // 64) * 64
+    brute, (rel,) = band_pair(irs, torch, w, dxy, dm, (r0, r0 + 64), [plan])
+    plan.close()
+    value = info.n_rays / (ms_map * 1e-3)
+    brute_ach = 10.0 * w["n_star"] * brute["rays"] / (brute["ms_raypass"] * 1e-3) / 1e12
+    return {"workload": w["name"], "value": value, "unit": "rays/s", "n_rays": int(info.n_rays),
+            "ms_per_map": ms_map, "ms_raypass": ms_ray,
+            "autotune": {"cell_mult": res.cell_mult, "kernel_variant": res.kernel_variant,
+                         "candidates": res.candidates, "tuning_s": tune_s},
+            "roofline": {"bound": "alu", "kernel": f"k_ip_ray variant {variant}", "achieved": ach,
+                         "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
+                         "flops_per_ray": flops, "mean_near_lenses": n_near},
+            "brute": dict(brute, roofline_frac=brute_ach / peak_tflops),
+            "speedup_over_brute": value / brute["rays_per_s"],
+            "map_rel_rms_vs_brute": rel, "min_rays_per_pixel": 100}
+
+
+def learned_record(irs, torch, lensgen, flush):
+    """The learned far field's workload (2e5 equal-mass lenses, 4000^2 map, 64
+    rays/px): the network trained on this lens field (untimed), whole-map
+    rays/s of the learned and of the series form, and each one's per-pixel
+    magnification rel RMS against the brute force on a 256-row band."""
+    w = WORKLOAD_LEARNED
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pm = workload_params(irs, "mlp", w)
+    plan = irs.Plan(pm)
+    info = plan.info
+    box = (info.lens_x0, info.lens_x1, info.lens_y0, info.lens_y1)
+    xy, m = lens_field(lensgen, box, w["seed"], w)
+    dxy, dm = torch.from_numpy(xy).to(dev), torch.from_numpy(m).to(dev)
+    rep = irs.irs_mlp_train(plan.handle, dxy, dm, seed=11)
+    pi = irs.Plan(workload_params(irs, "interp", w))
+    shape = (w["npix"], w["npix"])
+    counts = torch.zeros(shape, dtype=torch.uint32, device=dev)
+    mag = torch.zeros(shape, dtype=torch.float32, device=dev)
+    ms_mlp, _ = timed_maps(irs, torch, plan, dxy, dm, counts, mag, flush)
+    ms_int, _ = timed_maps(irs, torch, pi, dxy, dm, counts, mag, flush)
+    del counts, mag
+    r0 = (info.n_rays_y // 2 // 64) * 64
+    brute, (rel_mlp, rel_int) = band_pair(irs, torch, w, dxy, dm, (r0, r0 + 256), [plan, pi])
+    plan.close()
+    pi.close()
+    v_mlp, v_int = info.n_rays / (ms_mlp * 1e-3), info.n_rays / (ms_int * 1e-3)
+    return {"workload": w["name"], "n_rays": int(info.n_rays),
+            "network": {"samples": rep.samples, "steps": rep.steps, "heldout_rel_rms": rep.valid_rel_rms,
+                        "target_rms_thetaE": rep.target_rms, "loss_first": rep.loss_first,
+                        "loss_final": rep.loss_final, "ms_samples": rep.ms_samples, "ms_train": rep.ms_train},
+            "learned": {"value": v_mlp, "unit": "rays/s", "ms_per_map": ms_mlp,
+                        "map_rel_rms_vs_brute": rel_mlp, "speedup_over_brute": v_mlp / brute["rays_per_s"]},
+            "interp": {"value": v_int, "unit": "rays/s", "ms_per_map": ms_int,
+                       "map_rel_rms_vs_brute": rel_int, "speedup_over_brute": v_int / brute["rays_per_s"]},
+            "brute": brute, "bar_rel_rms": 1e-3, "min_rays_per_pixel": 100}
 
 
 def cpu_baseline(xy, m, w, target_s=15.0):
@@ -809,14 +958,19 @@ def batched_configs(n_maps=256, seed=4, max_rays=4.0e9):
 
 
 def study_batched(args):
-    """The batched persistent launch: 256 uneven maps through
+    """The batched persistent launch (see batched_measure), as its own JSON line."""
+    torch, irs, lensgen = _study_env()
+    print(json.dumps(batched_measure(torch, irs, lensgen, args.batch_maps, args.warmup, args.steps)))
+
+
+def batched_measure(torch, irs, lensgen, n_maps, warmup, steps):
+    """The batched persistent launch: n_maps uneven maps through
     irs_make_maps_batched (one captured CUDA graph, replayed), against one
     irs_make_map per map on the same plans; per-map and total rays/s, and a
     bitwise check that both give the same maps.  All plans use the setting
     the autotuner picks at the paper-mid workload (cells 0.85 x the rule,
     ray-pass variant 0), since one persistent launch serves one variant."""
-    torch, irs, lensgen = _study_env()
-    cfgs = batched_configs(args.batch_maps)
+    cfgs = batched_configs(n_maps)
     plans, lens, counts, rays = [], [], [], []
     ws = 0
     for k, c in enumerate(cfgs):
@@ -858,10 +1012,10 @@ def study_batched(args):
     # the batch: capture on the first call, then replays
     hs = [p.handle for p in plans]
     xs, ms_ = [x for x, _ in lens], [m for _, m in lens]
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         irs.irs_make_maps_batched(hs, xs, ms_, counts)
     torch.cuda.synchronize()
-    steps = max(args.steps, 1)
+    steps = max(steps, 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
@@ -883,7 +1037,7 @@ def study_batched(args):
            "maps_identical_to_single_calls": same, "workspace_gb": ws / 1e9}
     for p in plans:
         p.close()
-    print(json.dumps(out))
+    return out
 
 
 # ------------------------------------------------------------------ reference arm
@@ -938,6 +1092,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-brute", action="store_true", help="skip the brute-force band")
     ap.add_argument("--no-tune", action="store_true", help="paper-rule cells, default ray pass")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the high-res, learned and batched sub-records of the default run")
     ap.add_argument("--variant", type=int, default=-1, help="fixed kernel variant (skips tuning)")
     ap.add_argument("--cell-mult", type=float, default=0.0, help="with --variant: level-1 cell multiplier")
     ap.add_argument("--workload", default="", choices=["", "paper-mid", "high-res", "learned"],
