@@ -184,7 +184,7 @@ def ip_flops_fixed(variant):
 # dram__bytes_write.sum), valid only for the kernel build, workload and cell
 # size they were captured on: (workload, cell multiplier, variant) -> bytes.
 # Source: profiles/k_ip_ray_paper-mid-full.md.
-IP_TRAFFIC = {("paper-mid", 0.57, 0): 106.746112e6 + 3.398912e6}
+IP_TRAFFIC = {}
 
 
 def mean_near_lenses(info, xy):
@@ -1040,6 +1040,51 @@ def batched_measure(torch, irs, lensgen, n_maps, warmup, steps):
     return out
 
 
+def study_learned(args):
+    """The learned far field against its split radius R_f (cells): for each
+    R_f the network is trained on the learned workload's lens field, and the
+    study reports its held-out error, the deflection error that implies, the
+    map's per-pixel magnification rel RMS against a 256-row brute-force band,
+    and the map time; the series form on the same rays for comparison."""
+    torch, irs, lensgen = _study_env()
+    w = WORKLOAD_LEARNED
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    shape = (w["npix"], w["npix"])
+    counts = torch.zeros(shape, dtype=torch.uint32, device=dev)
+    pi = irs.Plan(workload_params(irs, "interp", w))
+    info = pi.info
+    box = (info.lens_x0, info.lens_x1, info.lens_y0, info.lens_y1)
+    xy, m = lens_field(lensgen, box, w["seed"], w)
+    dxy, dm = torch.from_numpy(xy).to(dev), torch.from_numpy(m).to(dev)
+    ms_int, _ = timed_maps(irs, torch, pi, dxy, dm, counts, None, flush)
+    r0 = (info.n_rays_y // 2 // 64) * 64
+    band = (r0, r0 + 256)
+    plans = [pi]
+    curve = []
+    for rf in args.rf_list:
+        pm = workload_params(irs, "mlp", w)
+        pm.window = int(rf)
+        plan = irs.Plan(pm)
+        rep = irs.irs_mlp_train(plan.handle, dxy, dm, seed=11)
+        ms, _ = timed_maps(irs, torch, plan, dxy, dm, counts, None, flush)
+        t = irs.irs_plan_timings(plan.handle)
+        curve.append({"rf_cells": int(rf), "rf_thetaE": rf * info.cell_x, "heldout_rel_rms": rep.valid_rel_rms,
+                      "target_rms_thetaE": rep.target_rms,
+                      "implied_deflection_error_thetaE": rep.valid_rel_rms * rep.target_rms,
+                      "ms_per_map": ms, "ms_far_field": float(t.ms_farfield), "ms_train": rep.ms_train,
+                      "ms_samples": rep.ms_samples})
+        plans.append(plan)
+    brute, rels = band_pair(irs, torch, w, dxy, dm, band, plans)
+    for c, r in zip(curve, rels[1:]):
+        c["map_rel_rms_vs_brute"] = r
+    for p in plans:
+        p.close()
+    print(json.dumps({"study": "learned", "workload": w["name"], "cell_thetaE": info.cell_x,
+                      "interp": {"ms_per_map": ms_int, "map_rel_rms_vs_brute": rels[0]},
+                      "brute": brute, "curve": curve, "bar_rel_rms": 1e-3}))
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     world, rank, local = dist_init()
@@ -1102,12 +1147,14 @@ def main():
     ap.add_argument("--n-star", type=int, default=0, help="override the lens count (profiling)")
     ap.add_argument("--npix", type=int, default=0, help="override the map side (profiling)")
     ap.add_argument("--nav", type=float, default=0.0, help="override rays per pixel (profiling)")
-    ap.add_argument("--study", default="", choices=["", "accuracy", "planes", "border", "batched"],
+    ap.add_argument("--study", default="", choices=["", "accuracy", "planes", "border", "batched", "learned"],
                     help="one of the paper's side measurements instead of the benchmark (one GPU)")
     ap.add_argument("--ref-rays", type=float, default=4.0e10, help="rays of the accuracy study's reference map")
     ap.add_argument("--ref-seconds", type=float, default=30.0,
                     help="--impl reference: host CPU seconds for the oracle's warm-up and timed steps together")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps of the batched study")
+    ap.add_argument("--rf-list", type=float, nargs="+", default=[4, 8, 16, 32],
+                    help="split radii R_f (cells) of the learned study")
     ap.add_argument("--shard", default="replicas", choices=["replicas", "strips"],
                     help="N > 1: a map per rank (weak scaling) or one map in row strips (strong)")
     args = ap.parse_args()
@@ -1115,7 +1162,7 @@ def main():
         args.warmup = 3
     if args.study:
         {"accuracy": study_accuracy, "planes": study_planes, "border": study_border,
-         "batched": study_batched}[args.study](args)
+         "batched": study_batched, "learned": study_learned}[args.study](args)
     elif args.impl == "reference":
         run_reference(args)
     else:

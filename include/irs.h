@@ -76,8 +76,11 @@ typedef struct irs_params {
                              the series; 0 = default */
   int32_t kernel_variant; /* INTERP: ray-pass variant 0..9 (rays per thread, level-2 sub-cells,
                              sub-cell terms, CTAs per SM, binning, shared reciprocals);
-                             irs_autotune picks one.  BRUTE: variant 0..9 (rows per thread,
-                             rows sharing a reciprocal, packed FP32x2 rows); 0 = default */
+                             irs_autotune picks one.  BRUTE: variant 0..13 (rows per thread,
+                             rows sharing a reciprocal by pairs or by fours, packed FP32x2
+                             rows); 0 = default.  Variants with four rows per reciprocal (0, 10,
+                             12..15) need a plane diagonal <= 1e4 theta_E
+                             (IRS_ERR_UNSUPPORTED otherwise) */
   int32_t reserved[6];    /* must be 0 */
 } irs_params;
 
@@ -287,7 +290,8 @@ irs_status irs_mlp_forward(irs_plan_t* plan, const float* x, int64_t n, float* y
  * scratch is a 7.9 MB file-scope device array that every GPU loading the
  * library holds until exit.  Limit: the ray lattice must fit 49,152 tiles of
  * 32 x 64 rays (about 1.0e8 rays); larger lattices return IRS_ERR_OVERFLOW
- * before any work is enqueued.  The first call on each device looks up the
+ * before any work is enqueued, and planes wider than 1e4 theta_E
+ * (diagonal) IRS_ERR_UNSUPPORTED.  The first call on each device looks up the
  * array's device address; where none of the library's device code has run on
  * that device yet, it also loads that code (CUDA loads modules lazily by
  * default), and the array is allocated then.  Make the first call on each

@@ -216,6 +216,8 @@ irs_status irs_plan(const irs_params* params, void* stream, irs_plan_t** out) {
   if (st == IRS_OK) st = alloc_workspace(P);
   if (st == IRS_OK && p.method == IRS_BRUTE && (p.kernel_variant < 0 || p.kernel_variant >= irs::brute_num_variants()))
     st = IRS_ERR_ARG;
+  if (st == IRS_OK && p.method == IRS_BRUTE && !irs::brute_variant_fits(p.kernel_variant, 2.0 * P->circle_r))
+    st = IRS_ERR_UNSUPPORTED;
   if (st == IRS_OK) P->br_grid = irs::brute_grid_size(P->num_sms, p.method == IRS_BRUTE ? p.kernel_variant : 0);
   if (st == IRS_OK && p.method != IRS_BRUTE) st = irs::interp_plan(P);
   if (st != IRS_OK) {

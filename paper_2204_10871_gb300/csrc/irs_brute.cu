@@ -3,13 +3,15 @@
 // Sec. 3.1), with the rectangular negative sheet of Eq. (alpha1) / Appendix A.
 //
 // Layout of the work: the ray lattice is cut into tiles of 32 x 64 rays.  A
-// CTA of 8 warps owns one tile at a time (persistent grid); lane l takes
-// column i0 + l and each warp 8 consecutive rows, so a thread carries 8 rays
-// that share their x offset.  Lenses stream through shared memory 256 at a
+// CTA of 64/R warps owns one tile at a time (persistent grid); lane l takes
+// column i0 + l and each warp R consecutive rows (R = 16 in the default
+// variant), so a thread carries R rays that share their x offset.  Lenses stream through shared memory 256 at a
 // time as FP32 positions relative to the tile centre (converted from the
 // caller's FP64 once per tile and stage) and are broadcast to all warps.
 //
-// Precision plan: per pair FP32 with rcp.approx on the SFU; each 256-lens
+// Precision plan: per pair FP32 with rcp.approx on the SFU (one reciprocal
+// per ray, or one per two or four rows of a column through products of
+// their squared distances); each 256-lens
 // stage is summed in FP32 and folded into a TwoSum (hi, lo) accumulator; the
 // sheet, the smooth terms and the pixel base of the tile centre are FP64 in
 // the setup kernel and reach the rays as double-float constants plus an
@@ -214,20 +216,38 @@ cudaError_t launch_brute_setup(const irs_plan_t* P, cudaStream_t s) {
 enum { MODE_MAP = 0, MODE_DUMP = 1 };
 
 // Variants: R rows per thread (the tile stays 32 x 64: 64/R warps per CTA),
-// PAIRED rows per thread that share one reciprocal per two rows, and PACK: the
+// PAIRED rows per thread that share one reciprocal per two rows, QUAD groups
+// of four packed rows that share one reciprocal per four rows, and PACK: the
 // other rows go two at a time through the packed FP32x2 instructions (the two
 // rows share dx and dx^2; fewer issue slots, the same FP32-pipe work).  The
 // TwoSum accumulators live in shared memory (updated once per 256-lens stage).
 // TPSM: resident threads per SM the register budget is sized for.
-// Variant 0 (the default) measured fastest: 59.8 % of the FP32 peak on a
-// 1e5-lens band against 58.1 % for variant 1, the fastest scalar form.
+//
+// Balance of the pair sum per lens and warp (32 lanes x R rows): the MUFU
+// unit takes 8 cycles per warp-wide reciprocal, the FP32 pipe 1 cycle per
+// scalar and 2 per packed instruction.  An unshared packed row pair costs 5
+// packed instructions (10 FP32 cycles) and 2 reciprocals (16 MUFU cycles); a
+// quad, two row pairs, 12 packed and 2 scalar instructions (26 FP32 cycles)
+// and 1 reciprocal (8 MUFU cycles):
+//   variant 11 (2 paired rows x 2, 6 packed pairs): MUFU 112, FP32  88 cycles
+//   variant 0 (1 quad, 6 packed pairs):             MUFU 104, FP32  90 cycles
+//   variant 10 (2 quads, 4 packed pairs):           MUFU  80, FP32  96 cycles
+// bounding the pair sum at 71, 77 and 83 % of the FP32 peak.  Measured on
+// the 1e5-lens band (one GB300, 2070 MHz): 59.7 % (variant 11), 62.3 %
+// (variant 0, the default), 60.6 % (variant 10): with two quads the FP32
+// pipe's longer dependent chains cost more than the MUFU cycles they save.
 #define BR_VARIANTS(X)                                                                         \
-  X(0, 16, 4, 1, 512) X(1, 16, 8, 0, 512) X(2, 8, 4, 0, 512) X(3, 8, 2, 0, 512)                 \
-  X(4, 16, 4, 0, 512) X(5, 16, 2, 0, 512) X(6, 16, 8, 1, 512) X(7, 16, 6, 1, 512)                \
-  X(8, 16, 2, 1, 512) X(9, 16, 4, 1, 640)
-constexpr int BR_NVARIANT = 10;
+  X(0, 16, 0, 1, 1, 512) X(1, 16, 8, 0, 0, 512) X(2, 8, 4, 0, 0, 512) X(3, 8, 2, 0, 0, 512)      \
+  X(4, 16, 4, 0, 0, 512) X(5, 16, 2, 0, 0, 512) X(6, 16, 8, 0, 1, 512) X(7, 16, 6, 0, 1, 512)     \
+  X(8, 16, 2, 0, 1, 512) X(9, 16, 4, 0, 1, 640) X(10, 16, 0, 2, 1, 512) X(11, 16, 4, 0, 1, 512)  \
+  X(12, 16, 0, 3, 1, 512) X(13, 8, 0, 1, 1, 512) X(14, 16, 2, 1, 1, 512) X(15, 16, 4, 1, 1, 512)
+constexpr int BR_NVARIANT = 16;
 
-template <int MODE, int R, int PAIRED, int PACK, int TPSM>
+// Plane diagonal (theta_E) up to which the four-row products of squared
+// distances stay inside the FP32 range with a wide margin ((1e4)^8 = 1e32).
+constexpr double BR_QUAD_MAX_DIAG = 1.0e4;
+
+template <int MODE, int R, int PAIRED, int QUAD, int PACK, int TPSM>
 __global__ void __launch_bounds__(32 * (BR_TY / R), TPSM / (32 * (BR_TY / R)))
 k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, int64_t n,
         const TileRec* __restrict__ recs, int64_t ntx, int64_t nwork, int64_t row0, int64_t row1,
@@ -235,7 +255,11 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
         double* __restrict__ beta_out, int64_t* __restrict__ pix_out) {
   constexpr int NT = 32 * (BR_TY / R);
   static_assert(PAIRED % 2 == 0 && (!PACK || (R - PAIRED) % 2 == 0), "rows go in pairs");
-  constexpr int NPK = PACK ? (R - PAIRED) / 2 : 0;  // packed row pairs
+  static_assert(QUAD == 0 || PACK, "quads are packed");
+  static_assert(PAIRED + 4 * QUAD <= R, "rows");
+  // packed row pairs after the PAIRED scalar rows: the first 2 QUAD of them
+  // form the quads
+  constexpr int NPK = PACK ? (R - PAIRED) / 2 : 0;
   // lens records: (x, y, m, 0) for the scalar form; with PACK, (-x, -x, -y, -y)
   // and (m, m) -- the duplicates feed the packed instructions and the scalar
   // rows read one half (t + (-x) == t - x)
@@ -340,9 +364,27 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
           pax[r + 1] = fmaf(wb, dx, pax[r + 1]);
           pay[r + 1] = fmaf(wb, dyb, pay[r + 1]);
         }
+        // quads: rows (a, b) and (c, d) as two packed pairs sharing one
+        // reciprocal of r_a^2 r_b^2 r_c^2 r_d^2; with P = (r_a^2 r_c^2, r_b^2 r_d^2)
+        // and Q = m/(r_a^2 r_b^2 r_c^2 r_d^2) (P.y, P.x), m/r^2 of (a, b) is
+        // Q (r_c^2, r_d^2) and of (c, d) is Q (r_a^2, r_b^2)
+#pragma unroll
+        for (int g4 = 0; g4 < QUAD; ++g4) {
+          const float2 DYa = __fadd2_rn(TYP[2 * g4], make_float2(L.z, L.w));
+          const float2 DYc = __fadd2_rn(TYP[2 * g4 + 1], make_float2(L.z, L.w));
+          const float2 R2a = __ffma2_rn(DYa, DYa, DX2), R2c = __ffma2_rn(DYc, DYc, DX2);
+          const float2 P4 = __fmul2_rn(R2a, R2c);
+          const float mR = M.x * rcp_approx(P4.x * P4.y);
+          const float2 Q4 = __fmul2_rn(make_float2(mR, mR), make_float2(P4.y, P4.x));
+          const float2 Wa = __fmul2_rn(Q4, R2c), Wc = __fmul2_rn(Q4, R2a);
+          PAX[2 * g4] = __ffma2_rn(Wa, DX, PAX[2 * g4]);
+          PAY[2 * g4] = __ffma2_rn(Wa, DYa, PAY[2 * g4]);
+          PAX[2 * g4 + 1] = __ffma2_rn(Wc, DX, PAX[2 * g4 + 1]);
+          PAY[2 * g4 + 1] = __ffma2_rn(Wc, DYc, PAY[2 * g4 + 1]);
+        }
         if (PACK) {
 #pragma unroll
-          for (int q = 0; q < NPK; ++q) {
+          for (int q = 2 * QUAD; q < NPK; ++q) {
             const float2 DY = __fadd2_rn(TYP[q], make_float2(L.z, L.w));
             const float2 R2 = __ffma2_rn(DY, DY, DX2);
             const float2 W = __fmul2_rn(M, make_float2(rcp_approx(R2.x), rcp_approx(R2.y)));
@@ -425,14 +467,30 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
   }
 }
 
-#define BR_DECL_OCC(V, R, PAIRED, PACK, TPSM)                                                   \
+#define BR_DECL_OCC(V, R, PAIRED, QUAD, PACK, TPSM)                                             \
   case V:                                                                                       \
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm,                                  \
-                                                      k_brute<MODE_MAP, R, PAIRED, PACK, TPSM>,  \
+                                                      k_brute<MODE_MAP, R, PAIRED, QUAD, PACK, TPSM>, \
                                                       32 * (BR_TY / R), 0) != cudaSuccess)      \
       per_sm = 1;                                                                               \
     break;
 int brute_num_variants() { return BR_NVARIANT; }
+
+#define BR_DECL_QUAD(V, R, PAIRED, QUAD, PACK, TPSM) \
+  case V:                                            \
+    return QUAD;
+static int brute_quads(int variant) {
+  switch (variant) { BR_VARIANTS(BR_DECL_QUAD) default: break; }
+  return 0;
+}
+
+// A variant with four-row reciprocals multiplies four squared distances: it
+// serves planes whose diagonal (the largest ray-lens distance; every lens is
+// inside the plane) keeps that product in the FP32 range.
+bool brute_variant_fits(int variant, double plane_diag) {
+  if (variant < 0 || variant >= BR_NVARIANT) return false;
+  return brute_quads(variant) == 0 || plane_diag <= BR_QUAD_MAX_DIAG;
+}
 
 int brute_grid_size(int num_sms, int variant) {
   int per_sm = 0;
@@ -440,13 +498,13 @@ int brute_grid_size(int num_sms, int variant) {
   return num_sms * (per_sm < 1 ? 1 : per_sm);
 }
 
-#define BR_DECL_LAUNCH(V, R, PAIRED, PACK, TPSM)                                               \
+#define BR_DECL_LAUNCH(V, R, PAIRED, QUAD, PACK, TPSM)                                         \
   case V:                                                                                      \
     if (mode == MODE_MAP)                                                                      \
-      k_brute<MODE_MAP, R, PAIRED, PACK, TPSM><<<(unsigned)grid, 32 * (BR_TY / R), 0, s>>>(    \
+      k_brute<MODE_MAP, R, PAIRED, QUAD, PACK, TPSM><<<(unsigned)grid, 32 * (BR_TY / R), 0, s>>>( \
           P->g, xy2, mass, n, P->d_tiles, P->br_ntx, nwork, row0, row1, counts, idx, beta, pix); \
     else                                                                                       \
-      k_brute<MODE_DUMP, R, PAIRED, PACK, TPSM><<<(unsigned)grid, 32 * (BR_TY / R), 0, s>>>(   \
+      k_brute<MODE_DUMP, R, PAIRED, QUAD, PACK, TPSM><<<(unsigned)grid, 32 * (BR_TY / R), 0, s>>>( \
           P->g, xy2, mass, n, P->d_tiles, P->br_ntx, nwork, row0, row1, counts, idx, beta, pix); \
     break;
 static cudaError_t launch_brute(const irs_plan_t* P, int mode, int64_t grid, const double* xy,

@@ -97,18 +97,23 @@ __device__ __forceinline__ bool pixel_from_rel(const Geo& g, int32_t ix, int32_t
   return true;
 }
 
-// Pixel key of a ray from its offset to the cell's base pixel (ix, iy) in
-// pixel units (t = beta_rel / s), floor per axis as in pixel_from_rel; ~0u if
-// the ray misses the map.  NaN rays fail the ordered test; +-Inf and huge
-// offsets saturate the conversion and, with |ix|, |iy| <= 1e9, cannot wrap
-// (mod 2^32) into range.
-__device__ __forceinline__ uint32_t pixel_key(float t1, float t2, int32_t ix, int32_t iy, int32_t npix_x,
-                                              int32_t npix_y) {
-  const bool num = !isnan(t1) && !isnan(t2);
-  const uint32_t px = (uint32_t)ix + (uint32_t)__float2int_rd(t1);
-  const uint32_t py = (uint32_t)iy + (uint32_t)__float2int_rd(t2);
-  const bool ok = num && px < (uint32_t)npix_x && py < (uint32_t)npix_y;
-  return ok ? py * (uint32_t)npix_x + px : 0xFFFFFFFFu;
+// Pixel keys of two rays at once.  (t + 1.5 2^23) rounded toward -inf keeps
+// floor(t) in its mantissa for |t| < 2^22: its bit pattern is
+// 0x4B400000 + floor(t).  So with the base folded in, bx = ix - 0x4B400000
+// (mod 2^32), the pixel index along an axis is bits + bx, and one unsigned
+// range test rejects every ray off the map: a NaN or infinite t and any
+// |t| >= 2^22 give a pattern that lands >= 8.7e8 away from the base, which
+// no map reaches (|ix|, npix < 2^22 -- a map of 4e6 pixels per side).
+constexpr float PIX_MAGIC = 12582912.0f;  // 1.5 2^23
+constexpr uint32_t PIX_MAGIC_BITS = 0x4B400000u;
+__device__ __forceinline__ void pixel_keys2(float2 t1, float2 t2, uint32_t bx, uint32_t by, uint32_t npix_x,
+                                            uint32_t npix_y, uint32_t& ka, uint32_t& kb) {
+  const float2 f1 = __fadd2_rd(t1, make_float2(PIX_MAGIC, PIX_MAGIC));
+  const float2 f2 = __fadd2_rd(t2, make_float2(PIX_MAGIC, PIX_MAGIC));
+  const uint32_t pxa = __float_as_uint(f1.x) + bx, pya = __float_as_uint(f2.x) + by;
+  const uint32_t pxb = __float_as_uint(f1.y) + bx, pyb = __float_as_uint(f2.y) + by;
+  ka = (pxa < npix_x && pya < npix_y) ? pya * npix_x + pxa : 0xFFFFFFFFu;
+  kb = (pxb < npix_x && pyb < npix_y) ? pyb * npix_x + pxb : 0xFFFFFFFFu;
 }
 
 // ---------------------------------------------------------------- brute force
@@ -207,6 +212,9 @@ cudaError_t launch_brute_dump(const irs_plan_t* P, const double* xy, const doubl
 cudaError_t launch_magnify(const irs_plan_t* P, const uint32_t* counts, float* mag, cudaStream_t s);
 int brute_grid_size(int num_sms, int variant);
 int brute_num_variants();
+// false when the variant's FP32 products of squared distances could leave the
+// FP32 range on a plane of this diagonal (theta_E), or the variant is unknown
+bool brute_variant_fits(int variant, double plane_diag);
 // FP64 sizing of the plane and lattice (irs_api.cu)
 irs_status size_plane(irs_plan_t* P);
 // the flow chart's level-1 cell side in ray spacings, before the cell

@@ -825,8 +825,10 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   }
   __syncthreads();
 
-  // base pixel of this cell for the 32-bit pixel test
+  // base pixel of this cell for the 32-bit pixel test, folded with the
+  // floor's bit pattern offset (pixel_keys2)
   const int32_t rix = rec_s.ix, riy = rec_s.iy;
+  const uint32_t rbx = (uint32_t)rix - PIX_MAGIC_BITS, rby = (uint32_t)riy - PIX_MAGIC_BITS;
   // the cell centre's beta (hi parts) in pixel units
   const float bxs = __fmul_rn(rec_s.bx_hi, g.inv_sx), bys = __fmul_rn(rec_s.by_hi, g.inv_sy);
   const int n_corner = rec_s.n_corner;
@@ -990,8 +992,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
         const float2 SY = __fadd2_rn(y0, __fadd2_rn(NAY[h + i], QI[i]));
         const float2 T1 = __ffma2_rn(SX, make_float2(g.inv_sx, g.inv_sx), make_float2(bxs, bxs));
         const float2 T2 = __ffma2_rn(SY, make_float2(g.inv_sy, g.inv_sy), make_float2(bys, bys));
-        key[2 * i] = pixel_key(T1.x, T2.x, rix, riy, g.npix_x, g.npix_y);
-        key[2 * i + 1] = pixel_key(T1.y, T2.y, rix, riy, g.npix_x, g.npix_y);
+        pixel_keys2(T1, T2, rbx, rby, (uint32_t)g.npix_x, (uint32_t)g.npix_y, key[2 * i], key[2 * i + 1]);
         if (MODE == IP_DUMP) {
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
@@ -1293,6 +1294,11 @@ irs_status interp_plan(irs_plan_t* P) {
     ex = ex < 0 ? 0 : ex;
     ey = ey < 0 ? 0 : ey;
   }
+  // the ray pass's pixel keys (pixel_keys2) need every ray that lands to be
+  // within 2^22 pixels of its cell's base pixel: maps below 2^21 pixels per
+  // side and protective borders below 2^20 pixels
+  if (g.npix_x >= (1 << 21) || g.npix_y >= (1 << 21) || P->border >= 1048576.0 * fmin(g.sx, g.sy))
+    return IRS_ERR_OVERFLOW;
   const int64_t ncx = ox + ig.nrcx + ex, ncy = oy + ig.nrcy + ey;
   if (ncx > FFT_MAX_LEN / 2 || ncy > FFT_MAX_LEN / 2) return IRS_ERR_OVERFLOW;
   ig.ncx = (int32_t)ncx;
@@ -1302,7 +1308,10 @@ irs_status interp_plan(irs_plan_t* P) {
   ig.gx0 = g.a1 - (double)ox * ig.h;
   ig.gy0 = g.b1 - (double)oy * ig.h;
   ig.K = p.far_order > 0 ? p.far_order : DEFAULT_K;
-  ig.W = p.window > 0 ? p.window : DEFAULT_W;
+  // `window` is the direct window of the series form; an IRS_MLP plan reads it
+  // as the learned split's radius R_f instead (its untrained fallback keeps
+  // the default window)
+  ig.W = (p.window > 0 && p.method != IRS_MLP) ? p.window : DEFAULT_W;
   ig.P = IP_P;
   if (ig.K > IP_KMAX || ig.K < 8) return IRS_ERR_ARG;
   ig.variant = p.kernel_variant;

@@ -4,8 +4,9 @@
 //
 // Split of the lens sum for a level-1 cell C with centre z_C (cell units r):
 //   near    the 3x3 block, per ray (unchanged);
-//   ring    every other lens with weight w(r), w = 1 for r <= R/2, cosine
-//           taper to 0 at R = R_f: summed directly into the cell series (FP64);
+//   ring    every other lens with weight w(r), w = 1 for r <= R/2, a C-infinity
+//           step to 0 at R = R_f (mlp_ring_weight): summed directly into the
+//           cell series (FP64);
 //   far-far every lens with weight 1 - w(r).  Its series, minus the sheet's
 //           analytic part g and the constant kappa_* conj(z_C) that the far
 //           continuum carries, is a smooth function U(z_C) of the cell centre
@@ -59,6 +60,7 @@ struct MlpState {
   double2* corner_pts;  // [ncorner] cell centres
   int64_t ncorner;
   double cx, cy, half;  // input normalisation: x = (z - centre) / half
+  double rf;            // window radius R_f in cells
   int trained;
   void* ws;
 };
@@ -120,8 +122,10 @@ __global__ void __launch_bounds__(FF_THREADS) k_ff_direct(const double2* __restr
       float wgt = m_s[j];
       if (r2 < R2) {
         if (r2 <= Rh2) continue;  // inside R/2: entirely in the direct ring
-        const float r = sqrtf(r2);
-        wgt *= 1.0f - 0.5f * (1.0f + cosf(3.14159265358979f * (2.0f * r / (float)R - 1.0f)));
+        // far-far share 1 - w of the ring weight (mlp_ring_weight)
+        const float t = 2.0f * sqrtf(r2) / (float)R - 1.0f;
+        const float ea = expf(-1.0f / t), eb = expf(-1.0f / (1.0f - t));
+        wgt *= ea / (ea + eb);
       }
       const float ir = rcp_approx(r2);
       const float ur = dx * ir, ui = -dy * ir;  // 1/d
@@ -547,7 +551,8 @@ irs_status mlp_plan(irs_plan_t* P, double gx0, double gy0, double h, int ncx, in
   // corner zones: ray cells whose centre lies within 1.5 R_f cells of a corner
   std::vector<int32_t> corner((size_t)nrc, -1);
   std::vector<double2> pts;
-  const double lim = 1.5 * MLP_RF * h;
+  M->rf = P->p.window > 0 ? (double)P->p.window : MLP_RF_DEFAULT;
+  const double lim = 1.5 * M->rf * h;
   const double cxs[4] = {P->g.a1, P->g.a2, P->g.a1, P->g.a2}, cys[4] = {P->g.b1, P->g.b1, P->g.b2, P->g.b2};
   for (int64_t rc = 0; rc < nrc; ++rc) {
     const double zx = gx0 + ((int)(rc % nrcx) + ox + 0.5) * h, zy = gy0 + ((int)(rc / nrcx) + oy + 0.5) * h;
@@ -631,7 +636,7 @@ irs_status mlp_prepare(irs_plan_t* P, const double* xy, const double* mass, int6
   const int64_t nrc = (int64_t)nrcx * nrcy;
   if (M->ncorner > 0 && n > 0)
     k_ff_direct<MLP_KEXACT><<<(unsigned)((M->ncorner + FF_THREADS - 1) / FF_THREADS), FF_THREADS, 0, s>>>(
-        reinterpret_cast<const double2*>(xy), mass, n, M->corner_pts, M->ncorner, h, MLP_RF, M->exact);
+        reinterpret_cast<const double2*>(xy), mass, n, M->corner_pts, M->ncorner, h, M->rf, M->exact);
   else if (M->ncorner > 0)
     cudaMemsetAsync(M->exact, 0, sizeof(double2) * MLP_KEXACT * M->ncorner, s);
   k_mlp_cell_inputs<<<(unsigned)((nrc + 255) / 256), 256, 0, s>>>(gx0, gy0, h, nrcx, ox, oy, nrc, M->cx, M->cy,
@@ -643,7 +648,7 @@ irs_status mlp_prepare(irs_plan_t* P, const double* xy, const double* mass, int6
   far->U = M->U;
   far->corner = M->corner;
   far->exact = M->exact;
-  far->rf = MLP_RF;
+  far->rf = M->rf;
   far->active = 1;
   return IRS_OK;
 }
@@ -740,7 +745,7 @@ irs_status mlp_train(irs_plan_t* P, const double* xy, const double* mass, int64_
     k_mlp_points<<<(unsigned)((n_all + 255) / 256), 256, 0, s>>>(P->g, seed * 0x9E3779B97F4A7C15ull + 1, n_all, pts);
     if (n > 0)
       k_ff_direct<MLP_KFF><<<(unsigned)((n_all + FF_THREADS - 1) / FF_THREADS), FF_THREADS, 0, s>>>(
-          reinterpret_cast<const double2*>(xy), mass, n, pts, n_all, h, MLP_RF, lff);
+          reinterpret_cast<const double2*>(xy), mass, n, pts, n_all, h, M->rf, lff);
     else
       cudaMemsetAsync(lff, 0, sizeof(double2) * MLP_KFF * n_all, s);
     // training inputs go to M->xs; the held-out ones follow in xv

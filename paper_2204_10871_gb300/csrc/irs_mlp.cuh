@@ -11,8 +11,9 @@ constexpr int MLP_OUT = 8;      // 4 complex series coefficients
 constexpr int MLP_NPARAM = 13000;
 constexpr int MLP_KFF = 4;      // far-far terms carried by the network
 constexpr int MLP_KEXACT = 12;  // far-far terms summed exactly for cells near the rectangle's corners
-constexpr double MLP_RF = 8.0;  // window radius in cells: lenses within R_f/2 are summed
-                                // directly in full, beyond R_f the network carries them
+constexpr double MLP_RF_DEFAULT = 8.0;  // window radius R_f in cells (irs_params.window of an
+                                        // IRS_MLP plan): lenses within R_f/2 are summed directly
+                                        // in full, beyond R_f the network carries them
 
 // What the far-field finalize needs from the network for one map.
 struct MlpFar {
@@ -23,11 +24,18 @@ struct MlpFar {
   int active;               // 1: the network replaces the FFT far field
 };
 
-// Lens weight of the direct ring: 1 inside R/2, 0 beyond R, cosine taper between (C^1).
+// Lens weight of the direct ring: 1 inside R/2, 0 beyond R, and between them
+// the C-infinity step w = b / (a + b), a = exp(-1/t), b = exp(-1/(1 - t)),
+// t = 2r/R - 1.  Flat at 1 near the cell, so lenses that enter or leave the
+// 3 x 3 near block as the cell moves never reach the far-far remainder, and
+// smooth to every order in between, so the remainder's spectrum has no
+// power-law tail from the taper.
 __device__ __forceinline__ double mlp_ring_weight(double r, double R) {
   if (r <= 0.5 * R) return 1.0;
   if (r >= R) return 0.0;
-  return 0.5 * (1.0 + cos(M_PI * (2.0 * r / R - 1.0)));
+  const double t = 2.0 * r / R - 1.0;
+  const double a = exp(-1.0 / t), b = exp(-1.0 / (1.0 - t));
+  return b / (a + b);
 }
 
 // host side (irs_mlp.cu)

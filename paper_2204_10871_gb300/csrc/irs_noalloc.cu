@@ -102,6 +102,7 @@ extern "C" irs_status irs_make_map_brute_noalloc(const irs_params* params, const
   P.br_nty = (P.g.nry + irs::BR_TY - 1) / irs::BR_TY;
   P.br_ntiles = P.br_ntx * P.br_nty;
   if (P.br_ntiles > NOALLOC_MAX_TILES) return IRS_ERR_OVERFLOW;  // lattice beyond the scratch
+  if (!irs::brute_variant_fits(0, 2.0 * P.circle_r)) return IRS_ERR_UNSUPPORTED;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IRS_ERR_CUDA;

@@ -79,13 +79,13 @@ def test_c1_sampled_deflection():
     assert np.mean(pg != po_pix) <= 2e-3
 
 
-BRUTE_VARIANTS = range(10)
+BRUTE_VARIANTS = range(16)
 
 
 @pytest.mark.parametrize("variant", BRUTE_VARIANTS)
 def test_every_brute_variant_meets_the_bars(variant):
-    """Each kernel variant (rows per thread, rows sharing a reciprocal, packed
-    rows, occupancy) against the FP64 oracle: the map (misbinned rays) and the
+    """Each kernel variant (rows per thread, rows sharing a reciprocal by
+    pairs or by fours, packed rows, occupancy) against the FP64 oracle: the map (misbinned rays) and the
     sampled deflections, with 400 lenses so that several shared-memory stages
     and their TwoSum folds are exercised."""
     torch = require_gpu()
@@ -215,7 +215,7 @@ def test_bad_arguments_raise():
             irs.irs_make_map(plan.handle, buf[1:], m, counts)
         with pytest.raises(ValueError):
             irs.irs_make_map(plan.handle, xy.float(), m, counts)
-    for method, bad in ((irs.IRS_BRUTE, 10), (irs.IRS_BRUTE, -1), (irs.IRS_INTERP, 10)):
+    for method, bad in ((irs.IRS_BRUTE, 16), (irs.IRS_BRUTE, -1), (irs.IRS_INTERP, 10)):
         _, p = params_pair(**C1, method=method, kernel_variant=bad)
         with pytest.raises(irs.IrsError):  # no such kernel variant
             irs.Plan(p)
