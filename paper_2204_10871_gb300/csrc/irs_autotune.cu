@@ -25,11 +25,11 @@
 #include <vector>
 
 #include "irs_common.cuh"
+#include "irs_interp.cuh"
 
 namespace {
 
 const double CELL_MULTS[] = {0.5, 0.6, 0.70710678, 0.85, 1.0, 1.2, 1.41421356, 2.0};
-constexpr int NVARIANT = 10;
 constexpr int STRIP_RAYS = 32;  // columns of a ray-pass work unit (one per lane)
 
 // Cell multipliers to try for a rule cell of `rule_rays` ray spacings.  The
@@ -194,7 +194,7 @@ extern "C" irs_status irs_autotune(const irs_params* params, const double* lens_
   }
   double best = -1.0;
   for (double m : cell_candidates(rule_rays)) {
-    for (int v = 0; v < NVARIANT; ++v) {
+    for (int v = 0; v < irs::interp_num_variants(); ++v) {
       const double t = measure(*params, m, v, lens_xy, mass, n, counts, h_rule, s);
       if (t < 0) continue;
       r.candidates++;

@@ -93,14 +93,17 @@ irs_status enqueue(BatchEntry* e, irs_plan_t* const* plans, int32_t nmaps, const
     // item count of the group, recomputed from the plans (cheap, host side)
     std::vector<irs_plan_t*> gp;
     std::vector<uint32_t*> gc;
+    int nrow = 0;
     for (int m : gm) {
       gp.push_back(plans[m]);
       gc.push_back(counts[m]);
+      const int r = irs::interp_row_entries(plans[m]);
+      nrow = r > nrow ? r : nrow;
     }
     std::vector<char> tmp(irs::interp_desc_bytes((int)gm.size()));
     const int64_t items = irs::interp_fill_descs(gp.data(), gc.data(), (int)gm.size(), tmp.data());
     irs_status st = irs::interp_batch_launch((int)v, base + group_off[v], (int)gm.size(), items,
-                                             queues + v, plans[gm[0]]->num_sms, cs);
+                                             queues + v, plans[gm[0]]->num_sms, nrow, cs);
     if (st != IRS_OK) return st;
   }
   if (mag) {
@@ -124,7 +127,7 @@ irs_status build_entry(BatchEntry* e, irs_plan_t* const* plans, int32_t nmaps,
     if (cudaEventCreateWithFlags(&e->ev[k], cudaEventDisableTiming) != cudaSuccess) return IRS_ERR_CUDA;
 
   // interpolated maps grouped by ray-pass variant; descriptors + queues in one buffer
-  std::vector<std::vector<int>> groups(10);
+  std::vector<std::vector<int>> groups(irs::interp_num_variants());
   for (int32_t m = 0; m < nmaps; ++m)
     if (plans[m]->p.method != IRS_BRUTE) groups[irs::interp_variant(plans[m])].push_back(m);
   std::vector<size_t> group_off(groups.size(), 0);

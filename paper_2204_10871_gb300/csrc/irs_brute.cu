@@ -309,7 +309,10 @@ k_brute(Geo g, const double2* __restrict__ xy, const double* __restrict__ mass, 
 #pragma unroll
       for (int q = 0; q < BR_LT / NT; ++q) {
         const int64_t k = base + q * NT + tid;
-        v[q] = make_float4(1.0e15f, 1.0e15f, 0.f, 0.f);  // padding: massless, far away
+        // padding: massless, and far enough that it is never on a ray, near
+        // enough that products of four squared distances stay finite (a
+        // product overflowing to inf would turn 0 x inf into NaN)
+        v[q] = make_float4(4096.f, 4096.f, 0.f, 0.f);
         if (k < n) {
           const double2 p = xy[k];
           v[q] = make_float4((float)(p.x - zx), (float)(p.y - zy), (float)mass[k], 0.f);

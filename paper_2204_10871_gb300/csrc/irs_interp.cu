@@ -88,6 +88,8 @@ struct IpGeo {
   int variant;  // ray-pass kernel variant (R, Q, K2)
   float hf;     // (float) h
   float inv_k;  // 1 / k in FP32 (correctly rounded)
+  int32_t nrow;  // row-pair entries of the ray pass's row table: (k + 1)/2 + IP_ROW_PAD
+  int32_t pad_;
 };
 
 struct InterpState {
@@ -635,8 +637,8 @@ struct IpRayArgs {
   X(0, 8, 12, 6, 3, 0, 0) X(1, 8, 10, 7, 3, 0, 0) X(2, 8, 16, 6, 3, 0, 2)                       \
   X(3, 8, 16, 6, 3, 0, 4) X(4, 8, 16, 6, 2, 1, 0) X(5, 8, 16, 6, 3, 1, 0)                      \
   X(6, 8, 16, 6, 3, 1, 2) X(7, 8, 16, 6, 3, 0, 0) X(8, 4, 16, 6, 4, 0, 0)                      \
-  X(9, 8, 8, 8, 3, 0, 0)
-constexpr int IP_NVARIANT = 10;
+  X(9, 8, 8, 8, 3, 0, 0) X(10, 8, 12, 6, 4, 0, 0)
+constexpr int IP_NVARIANT = 11;
 
 // Advance a (strip, row group) position by `by` units of a row-major
 // nstrip-wide unit grid.
@@ -667,15 +669,20 @@ constexpr int IP_CB_STRIDE = IP_KMAX + 1;
 // near lenses as (-x, -x, -y, -y) and (-m, -m) pairs, the level-2 series
 // as conj duplicated (c.re, c.re, -c.im, -c.im), the row table and the
 // level-1 series scaled for the re-centring, one row per level-2 term.
+// The row table holds `nrow` entries, sized per plan from its cell side
+// (IpGeo::nrow), so that small cells leave shared memory for more CTAs.
 template <int Q, int K2>
 struct IpSmem {
   static constexpr size_t near_xy = 0;
   static constexpr size_t near_m = near_xy + sizeof(float4) * IP_NEAR_MAX;
   static constexpr size_t sub = near_m + sizeof(float2) * IP_NEAR_MAX;
-  static constexpr int nrow = IP_KMAX_RAYS / 2 + IP_ROW_PAD;
+  static constexpr int nrow_max = IP_KMAX_RAYS / 2 + IP_ROW_PAD;
   static constexpr size_t row_sg = sub + sizeof(float4) * Q * Q * K2;
-  static constexpr size_t coef = row_sg + sizeof(IpRowPair) * nrow;
-  static constexpr size_t bytes = (coef + sizeof(float2) * K2 * IP_CB_STRIDE + 15) / 16 * 16;
+  static __host__ __device__ constexpr size_t coef(int nrow) { return row_sg + sizeof(IpRowPair) * nrow; }
+  static __host__ __device__ constexpr size_t bytes(int nrow) {
+    return (coef(nrow) + sizeof(float2) * K2 * IP_CB_STRIDE + 15) / 16 * 16;
+  }
+  static constexpr size_t bytes_max = bytes(nrow_max);
 };
 
 // One level-1 cell: gather the 3x3 block's lenses, re-centre the series on the
@@ -698,7 +705,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   float2* nm_s = reinterpret_cast<float2*>(ip_smem + L::near_m);
   float4* sub_s = reinterpret_cast<float4*>(ip_smem + L::sub);
   IpRowPair* row_s = reinterpret_cast<IpRowPair*>(ip_smem + L::row_sg);
-  float2* cb_s = reinterpret_cast<float2*>(ip_smem + L::coef);
+  float2* cb_s = reinterpret_cast<float2*>(ip_smem + L::coef(ig.nrow));
   __shared__ CellRec rec_s;
   __shared__ int blk_start[9], blk_off[10];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -785,21 +792,28 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     nxy_s[t] = make_float4(-x, -x, -y, -y);
     nm_s[t] = make_float2(-v.z, -v.z);
   }
-  // then per (sub-cell, n) the polynomial sum_j cb[n][n + j] eps^j by Horner
-  for (int t = tid; t < Q * Q * K2; t += blockDim.x) {
-    const int sub = t / K2, nn = t % K2;
-    const float er = __fmaf_rn(__fadd_rn((float)(sub % Q), 0.5f), inv_q, -0.5f);
-    const float ei = __fmaf_rn(__fadd_rn((float)(sub / Q), 0.5f), inv_q, -0.5f);
+  // then per (sub-cell, n) the polynomial sum_j cb[n][n + j] eps^j by Horner,
+  // two sub-cells of one sub-cell row at a time (Q is even) through packed
+  // FP32x2 instructions: the same roundings as two scalar Horner chains
+  static_assert(Q % 2 == 0, "sub-cells go in pairs along a row");
+  for (int t = tid; t < Q * Q * K2 / 2; t += blockDim.x) {
+    const int sp = t / K2, nn = t % K2;
+    const int sa = 2 * sp;  // sub-cells sa, sa + 1: same row, adjacent columns
+    const float er_a = __fmaf_rn(__fadd_rn((float)(sa % Q), 0.5f), inv_q, -0.5f);
+    const float er_b = __fmaf_rn(__fadd_rn((float)(sa % Q + 1), 0.5f), inv_q, -0.5f);
+    const float ei = __fmaf_rn(__fadd_rn((float)(sa / Q), 0.5f), inv_q, -0.5f);
+    const float2 ER = make_float2(er_a, er_b), EI = make_float2(ei, ei), NEI = make_float2(-ei, -ei);
     const float2* cb = cb_s + nn * IP_CB_STRIDE;
-    float sr = 0.f, si = 0.f;
+    float2 SR = make_float2(0.f, 0.f), SI = make_float2(0.f, 0.f);
 #pragma unroll 2
     for (int kk = ig.K - 1; kk >= nn; --kk) {
       const float2 c = cb[kk];
-      const float nr = __fmaf_rn(sr, er, __fmaf_rn(-si, ei, c.x));
-      si = __fmaf_rn(sr, ei, __fmaf_rn(si, er, c.y));
-      sr = nr;
+      const float2 NR = __ffma2_rn(SR, ER, __ffma2_rn(SI, NEI, make_float2(c.x, c.x)));
+      SI = __ffma2_rn(SR, EI, __ffma2_rn(SI, ER, make_float2(c.y, c.y)));
+      SR = NR;
     }
-    sub_s[t] = make_float4(sr, sr, -si, -si);
+    sub_s[sa * K2 + nn] = make_float4(SR.x, SR.x, -SI.x, -SI.x);
+    sub_s[(sa + 1) * K2 + nn] = make_float4(SR.y, SR.y, -SI.y, -SI.y);
   }
   // row table: t_y = tau_y h, sigma_y = (l + 1/2) Q / k - v - 1/2, v Q, rows of
   // the whole cell side in pairs and R / 2 pairs past it (rows past the cell
@@ -1083,7 +1097,7 @@ k_ip_ray_batch(const MapDesc* __restrict__ maps, int nmaps, int64_t nitems,
 // before any launch or graph capture that uses it.
 #define IP_DECL_ATTR(V, R, Q, K2, MINB, BIN, NPR)                                                           \
   case V: {                                                                                            \
-    const int b = (int)IpSmem<Q, K2>::bytes;                                                          \
+    const int b = (int)IpSmem<Q, K2>::bytes_max;                                                      \
     e = cudaFuncSetAttribute(k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR>,                                   \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, b);                         \
     if (e == cudaSuccess)                                                                              \
@@ -1103,21 +1117,31 @@ cudaError_t ip_ray_attributes(int variant) {
 #define IP_DECL_OCC(V, R, Q, K2, MINB, BIN, NPR)                                                       \
   case V:                                                                                         \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR>, \
-                                                  IP_THREADS, IpSmem<Q, K2>::bytes);              \
+                                                  IP_THREADS, IpSmem<Q, K2>::bytes(nrow));        \
     break;
-int ip_ray_occupancy(int variant) {
+// CTAs per SM of a variant whose row table has `nrow` entries
+int ip_ray_occupancy(int variant, int nrow) {
   int per_sm = 0;
   switch (variant) { IP_VARIANTS(IP_DECL_OCC) default: break; }
   return per_sm > 0 ? per_sm : 1;
 }
 
+#define IP_DECL_BYTES(V, R, Q, K2, MINB, BIN, NPR) \
+  case V:                                          \
+    return IpSmem<Q, K2>::bytes(nrow);
+size_t ip_ray_smem(int variant, int nrow) {
+  switch (variant) { IP_VARIANTS(IP_DECL_BYTES) default: break; }
+  return 0;
+}
+
 #define IP_DECL_LAUNCH(V, R, Q, K2, MINB, BIN, NPR)                                                           \
   case V:                                                                                                \
     if (mode == IP_MAP)                                                                                  \
-      k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(g, ig, \
-                                                                                                   a);   \
+      k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes(ig.nrow), \
+                                                   s>>>(g, ig, a);                                           \
     else                                                                                                 \
-      k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(g,    \
+      k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes(ig.nrow), \
+                                                    s>>>(g,                                                  \
                                                                                                  ig, a); \
     break;
 cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, const Geo& g,
@@ -1128,11 +1152,11 @@ cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, c
 
 #define IP_DECL_BATCH(V, R, Q, K2, MINB, BIN, NPR)                                                       \
   case V:                                                                                           \
-    k_ip_ray_batch<R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes, s>>>(   \
+    k_ip_ray_batch<R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes(nrow), s>>>( \
         maps, nmaps, nitems, queue);                                                                \
     break;
 cudaError_t launch_ip_ray_batch(int variant, int64_t grid, cudaStream_t s, const MapDesc* maps,
-                                int nmaps, int64_t nitems, unsigned long long* queue) {
+                                int nmaps, int64_t nitems, unsigned long long* queue, int nrow) {
   switch (variant) { IP_VARIANTS(IP_DECL_BATCH) default: return cudaErrorInvalidValue; }
   return cudaGetLastError();
 }
@@ -1276,6 +1300,7 @@ irs_status interp_plan(irs_plan_t* P) {
   if (k < 4) k = 4;
   if (k > IP_KMAX_RAYS) k = IP_KMAX_RAYS;  // the ray pass keeps a row table per cell
   ig.k = k;
+  ig.nrow = (int32_t)((k + 1) / 2) + IP_ROW_PAD;
   ig.h = (double)k * g.dx3;
   ig.hf = (float)ig.h;
   ig.inv_k = 1.0f / (float)k;
@@ -1375,7 +1400,7 @@ irs_status interp_plan(irs_plan_t* P) {
   if (fft2d_forward(S->kspec_f, f.Nx, f.Ny, G, S->kspec_f, f, nker, 0) != cudaSuccess) return IRS_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return IRS_ERR_CUDA;
   if (ip_ray_attributes(ig.variant) != cudaSuccess) return IRS_ERR_CUDA;
-  S->grid_ray = P->num_sms * ip_ray_occupancy(ig.variant);
+  S->grid_ray = P->num_sms * ip_ray_occupancy(ig.variant, ig.nrow);
   if (p.method == IRS_MLP) {
     if (p.plane != IRS_PLANE_RECT) return IRS_ERR_UNSUPPORTED;
     irs_status st2 = mlp_plan(P, ig.gx0, ig.gy0, ig.h, ig.ncx, ig.ncy, ig.nrcx, ig.nrcy, ig.ox, ig.oy, 1 << 20);
@@ -1458,6 +1483,8 @@ irs_status interp_prepare(irs_plan_t* P, const double* xy, const double* mass, i
 }
 
 int interp_variant(const irs_plan_t* P) { return S_(P)->ig.variant; }
+int interp_row_entries(const irs_plan_t* P) { return S_(P)->ig.nrow; }
+int interp_num_variants() { return IP_NVARIANT; }
 
 size_t interp_desc_bytes(int nmaps) { return sizeof(MapDesc) * (size_t)(nmaps > 0 ? nmaps : 1); }
 
@@ -1482,13 +1509,13 @@ int64_t interp_fill_descs(irs_plan_t* const* plans, uint32_t* const* counts, int
 }
 
 irs_status interp_batch_launch(int variant, const void* dev_descs, int nmaps, int64_t nitems,
-                               unsigned long long* queue, int num_sms, cudaStream_t s) {
+                               unsigned long long* queue, int num_sms, int nrow, cudaStream_t s) {
   if (nmaps <= 0 || nitems <= 0) return IRS_OK;
-  int64_t grid = (int64_t)num_sms * ip_ray_occupancy(variant);
+  int64_t grid = (int64_t)num_sms * ip_ray_occupancy(variant, nrow);
   if (grid > nitems) grid = nitems;
   if (cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return IRS_ERR_CUDA;
   return launch_ip_ray_batch(variant, grid, s, static_cast<const MapDesc*>(dev_descs), nmaps, nitems,
-                             queue) == cudaSuccess
+                             queue, nrow) == cudaSuccess
              ? IRS_OK
              : IRS_ERR_CUDA;
 }

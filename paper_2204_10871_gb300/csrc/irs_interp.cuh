@@ -24,11 +24,15 @@ irs_status interp_ensure_capacity(irs_plan_t* P, int64_t n);
 irs_status interp_prepare(irs_plan_t* P, const double* xy, const double* mass, int64_t n,
                           cudaStream_t s);
 int interp_variant(const irs_plan_t* P);
+// row-table entries of the plan's ray pass (shared memory per CTA grows with them)
+int interp_row_entries(const irs_plan_t* P);
+int interp_num_variants();
 // host-side ray-pass descriptors of maps that share a kernel variant; returns
 // the total number of (map, cell) work items
 size_t interp_desc_bytes(int nmaps);
 int64_t interp_fill_descs(irs_plan_t* const* plans, uint32_t* const* counts, int nmaps, void* host);
-// one persistent launch over all maps' cells (descriptors already on the device)
+// one persistent launch over all maps' cells (descriptors already on the
+// device); nrow: the largest row table among the maps
 irs_status interp_batch_launch(int variant, const void* dev_descs, int nmaps, int64_t nitems,
-                               unsigned long long* queue, int num_sms, cudaStream_t s);
+                               unsigned long long* queue, int num_sms, int nrow, cudaStream_t s);
 }  // namespace irs

@@ -86,12 +86,13 @@ BRUTE_VARIANTS = range(16)
 def test_every_brute_variant_meets_the_bars(variant):
     """Each kernel variant (rows per thread, rows sharing a reciprocal by
     pairs or by fours, packed rows, occupancy) against the FP64 oracle: the map (misbinned rays) and the
-    sampled deflections, with 400 lenses so that several shared-memory stages
-    and their TwoSum folds are exercised."""
+    sampled deflections, with 403 lenses so that several shared-memory stages
+    and their TwoSum folds are exercised and the last stage carries massless
+    padding lenses (its count rounded up to a multiple of 8)."""
     torch = require_gpu()
     po, pl = params_pair(**C1, kernel_variant=variant)
     qo = oracle.size(po)
-    xy, m = lenses_for(qo, 400, seed=5, kappa_star=0.3)
+    xy, m = lenses_for(qo, 403, seed=5, kappa_star=0.3)
     qo, co, mo, landed, cg, mg = _map_pair(torch, po, pl, xy, m)
     bad = misbinned(co, cg)
     assert bad <= MISBIN_TOL * landed, f"{bad} of {landed} rays binned differently"
@@ -215,7 +216,7 @@ def test_bad_arguments_raise():
             irs.irs_make_map(plan.handle, buf[1:], m, counts)
         with pytest.raises(ValueError):
             irs.irs_make_map(plan.handle, xy.float(), m, counts)
-    for method, bad in ((irs.IRS_BRUTE, 16), (irs.IRS_BRUTE, -1), (irs.IRS_INTERP, 10)):
+    for method, bad in ((irs.IRS_BRUTE, 16), (irs.IRS_BRUTE, -1), (irs.IRS_INTERP, 11)):
         _, p = params_pair(**C1, method=method, kernel_variant=bad)
         with pytest.raises(irs.IrsError):  # no such kernel variant
             irs.Plan(p)
