@@ -627,7 +627,9 @@ struct IpRayArgs {
 // rays per thread R, level-2 sub-cells per side Q, sub-cell series terms K2.
 // The truncation is (sub-cell half-diagonal / distance to the nearest far
 // lens)^K2 of that lens's field: Q = 8, 10, 12, 16 give ratios 0.083, 0.067,
-// 0.057, 0.042, so 8, 7, 6 and 6 terms stay at or below ~3e-8.
+// 0.057, 0.042, so 8, 7, 6 and 6 terms stay at or below ~3e-8; variant 11
+// trades one Horner step per ray for a bound of 1.7e-7 (16 sub-cells, 5
+// terms).
 // MINB: CTAs per SM the register budget is sized for; BIN: warp binning by
 // __match_any_sync (0) or by runs of equal pixels (1); NPR: how many of a
 // thread's R/2 row pairs share one reciprocal per lens, 1/(r_a^2 r_b^2) (the
@@ -637,8 +639,8 @@ struct IpRayArgs {
   X(0, 8, 12, 6, 3, 0, 0) X(1, 8, 10, 7, 3, 0, 0) X(2, 8, 16, 6, 3, 0, 2)                       \
   X(3, 8, 16, 6, 3, 0, 4) X(4, 8, 16, 6, 2, 1, 0) X(5, 8, 16, 6, 3, 1, 0)                      \
   X(6, 8, 16, 6, 3, 1, 2) X(7, 8, 16, 6, 3, 0, 0) X(8, 4, 16, 6, 4, 0, 0)                      \
-  X(9, 8, 8, 8, 3, 0, 0) X(10, 8, 12, 6, 4, 0, 0)
-constexpr int IP_NVARIANT = 11;
+  X(9, 8, 8, 8, 3, 0, 0) X(10, 8, 12, 6, 4, 0, 0) X(11, 8, 16, 5, 3, 0, 0)
+constexpr int IP_NVARIANT = 12;
 
 // Advance a (strip, row group) position by `by` units of a row-major
 // nstrip-wide unit grid.
