@@ -727,47 +727,80 @@ def _interp_map(irs, torch, params, dxy, dm, rows=None):
 
 
 def study_accuracy(args):
-    """Sec. 3.3: kappa = kappa_* = 0.652, gamma = 0, 50 theta_E at 1024^2, 1e5
-    uniform-mass lenses; maps of (10240 k)^2 rays, k = 1..7, against a map of
-    ~4e10 rays; RMS relative magnification error in 300 log bins of the
-    per-pixel ray count, and its log-log slope (paper: about -2/3)."""
+    """Sec. 3.3 replayed at the paper's shape (see accuracy_replay)."""
     torch, irs, lensgen = _study_env()
-    ks, S, npix = 0.652, 50.0, 1024
+    print(json.dumps(accuracy_replay(torch, irs, lensgen, ref_rays=args.ref_rays, reference=args.accuracy_ref)))
+
+
+def accuracy_replay(torch, irs, lensgen, ks=0.652, S=50.0, npix=1024, n_star=100000, ref_rays=4.0e10,
+                    test_rays=tuple((10240 * k) ** 2 for k in range(1, 8)), reference="brute",
+                    ref_chunk_rays=2.0e9, seed=7, fit_min=10.0):
+    """Sec. 3.3: kappa = kappa_* = 0.652, gamma = 0, S = 50 theta_E at 1024^2,
+    1e5 uniform-mass lenses; interpolated maps of (10240 k)^2 rays, k = 1..7,
+    against a reference map of ~4e10 rays made by the brute force (ordinary
+    IRS, the paper's criterion; shot in bands of lattice rows) or by the
+    interpolated method; RMS relative magnification error in 300 log bins of
+    the per-pixel ray count, and its log-log slope (paper: about -2/3).  With
+    the brute-force reference the interpolated map of the same rays is also
+    compared with it (whole-map rel RMS over pixels with >= 100 rays)."""
     src = (-S / 2, S / 2, -S / 2, S / 2)
-    n_star = 100000
-    base = irs.make_params(ks, 0.0, 0.0, src, npix, 1.0, n_star=n_star, method=irs.IRS_INTERP)
-    with irs.Plan(base) as pr:
+    s2 = (S / npix) ** 2
+    # Every map's lattice tiles the same plane: the flow chart's side
+    # I = (S + 2P)/(1 - kappa) (gamma = 0: a square) split into n rays per
+    # side, i.e. n^2 rays at s^2 n^2 / I^2 rays per unlensed pixel.  One lens
+    # field then fills every map's lens plane and gives each map the same
+    # sheet density.
+    side = (S + 20.0 * np.sqrt(ks)) / (1.0 - ks)
+
+    def nav_for(n_rays):
+        n = round(np.sqrt(n_rays))
+        return s2 * n * n / (side * side)
+
+    def params(n_rays, method=irs.IRS_INTERP):
+        return irs.make_params(ks, 0.0, 0.0, src, npix, nav_for(n_rays), n_star=n_star, method=method,
+                               kernel_variant=7 if method == irs.IRS_INTERP else 0)
+
+    with irs.Plan(params(ref_rays)) as pr:
         inf = pr.info
     box = (inf.lens_x0, inf.lens_x1, inf.lens_y0, inf.lens_y1)
     area = (box[1] - box[0]) * (box[3] - box[2])
-    xy, m = lensgen.lens_field(n_star, box, shape="uniform", seed=7, total_mass=ks * area / np.pi)
+    xy, m = lensgen.lens_field(n_star, box, shape="uniform", seed=seed, total_mass=ks * area / np.pi)
     dxy, dm = torch.from_numpy(xy).cuda(), torch.from_numpy(m).cuda()
-    s2 = (S / npix) ** 2
-
-    def params(n_rays, method=irs.IRS_INTERP):
-        return irs.make_params(ks, 0.0, 0.0, src, npix, n_rays * s2 / area, n_star=n_star, method=method,
-                               kernel_variant=7 if method == irs.IRS_INTERP else 0)
-
-    ref_rays = args.ref_rays
-    ref, tref, iref = _interp_map(irs, torch, params(ref_rays), dxy, dm)
-    nav_ref = ref_rays * s2 / area
-    # the reference's own method error: the brute force on a band of its rays
-    r0 = iref.n_rays_y // 2
-    band = (r0, r0 + 64)
-    pb = params(ref_rays, irs.IRS_BRUTE)
-    bb, _, _ = _interp_map(irs, torch, pb, dxy, dm, rows=band)
-    bi, _, _ = _interp_map(irs, torch, params(ref_rays), dxy, dm, rows=band)
-    sel = bb >= 100
-    band_rms = float(np.sqrt(np.mean(((bi[sel] - bb[sel]) / bb[sel]) ** 2))) if sel.any() else None
+    nav_ref = nav_for(ref_rays)
+    ri, tri, iref = _interp_map(irs, torch, params(ref_rays), dxy, dm)
+    ref_info = {"n_rays": int(iref.n_rays), "rays_per_unlensed_pixel": nav_ref, "method": reference}
+    if reference == "brute":
+        shape = (npix, npix)
+        cb = torch.zeros(shape, dtype=torch.uint32, device=dxy.device)
+        with irs.Plan(params(ref_rays, irs.IRS_BRUTE)) as pb:
+            ny, nx = pb.info.n_rays_y, pb.info.n_rays_x
+            step = max(64, int(ref_chunk_rays / nx) // 64 * 64)  # whole brute-force tiles
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for r0 in range(0, ny, step):
+                irs.irs_make_map_rows(pb.handle, dxy, dm, r0, min(ny, r0 + step), cb)
+            e1.record()
+            pb.sync()
+            ref_info["ms_map"] = e0.elapsed_time(e1)
+            ref_info["bands"] = (ny + step - 1) // step
+        ref = cb.cpu().numpy().astype(np.float64)
+        sel = ref >= 100
+        r = (ri[sel] - ref[sel]) / ref[sel]
+        ref_info["interp_same_rays_rel_rms"] = float(np.sqrt(np.mean(r * r))) if sel.any() else None
+        ref_info["pixels_ge_100_rays"] = int(sel.sum())
+        ref_info["interp_ms_map"] = tri.ms_total
+    else:
+        ref = ri
+        ref_info["ms_map"] = tri.ms_total
     maps, allx, ally, allw = [], [], [], []
-    for k in range(1, 8):
-        n_rays = (10240 * k) ** 2
+    for n_rays in test_rays:
         c, t, info = _interp_map(irs, torch, params(n_rays), dxy, dm)
-        nav = n_rays * s2 / area
+        nav = nav_for(n_rays)
+        assert abs(info.lens_x1 - info.lens_x0 - (box[1] - box[0])) <= 1e-9 * side  # the same plane
         ok = ref > 0
         err = (c[ok] / nav) / (ref[ok] / nav_ref) - 1.0
         x, y, w = log_binned_rms(c[ok], err, nbins=300, n_max=None, min_count=30)
-        fit = x >= 10
+        fit = x >= fit_min
         maps.append({"n_rays_target": n_rays, "n_rays": int(info.n_rays), "rays_per_unlensed_pixel": nav,
                      "mean_rays_per_pixel": float(c.mean()), "ms_map": t.ms_total,
                      "rel_rms_all_pixels": float(np.sqrt(np.mean(err[c[ok] > 0] ** 2))),
@@ -775,15 +808,12 @@ def study_accuracy(args):
                      "bins": int(len(x))})
         allx.append(x[fit]); ally.append(y[fit]); allw.append(w[fit])
     X, Y, Wt = np.concatenate(allx), np.concatenate(ally), np.concatenate(allw)
-    out = {"study": "accuracy", "config": {"kappa": ks, "kappa_star": ks, "gamma": 0.0, "S": S, "npix": npix,
-                                           "n_star": n_star, "masses": "uniform 0.1-1 rescaled to kappa_*",
-                                           "method": "interp variant 7", "bins": 300, "min_pixels_per_bin": 30,
-                                           "fit": "bins with >= 10 rays per pixel"},
-           "reference": {"n_rays": int(iref.n_rays), "rays_per_unlensed_pixel": nav_ref, "ms_map": tref.ms_total,
-                         "interp_vs_brute_band_rel_rms": band_rms, "band_rows": list(band),
-                         "band_pixels_ge_100_rays": int(sel.sum())},
-           "maps": maps, "slope_all_maps": loglog_slope(X, Y, Wt), "paper_slope": -2.0 / 3.0}
-    print(json.dumps(out))
+    return {"study": "accuracy", "config": {"kappa": ks, "kappa_star": ks, "gamma": 0.0, "S": S, "npix": npix,
+                                            "n_star": n_star, "masses": "uniform 0.1-1 rescaled to kappa_*",
+                                            "method": "interp variant 7", "bins": 300, "min_pixels_per_bin": 30,
+                                            "fit": f"bins with >= {fit_min:g} rays per pixel"},
+            "reference": ref_info, "maps": maps,
+            "slope_all_maps": loglog_slope(X, Y, Wt) if len(X) > 2 else None, "paper_slope": -2.0 / 3.0}
 
 
 def study_planes(args):
@@ -1150,6 +1180,8 @@ def main():
     ap.add_argument("--study", default="", choices=["", "accuracy", "planes", "border", "batched", "learned"],
                     help="one of the paper's side measurements instead of the benchmark (one GPU)")
     ap.add_argument("--ref-rays", type=float, default=4.0e10, help="rays of the accuracy study's reference map")
+    ap.add_argument("--accuracy-ref", default="brute", choices=["brute", "interp"],
+                    help="method of the accuracy study's reference map (the paper's criterion is brute force)")
     ap.add_argument("--ref-seconds", type=float, default=30.0,
                     help="--impl reference: host CPU seconds for the oracle's warm-up and timed steps together")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps of the batched study")

@@ -56,3 +56,24 @@ def test_log_binned_rms_recovers_the_error_slope():
     assert len(x) > 100
     fit = x >= 10
     assert bench.loglog_slope(x[fit], y[fit], w[fit]) == pytest.approx(-0.75, abs=0.02)
+
+
+@pytest.mark.gpu
+def test_accuracy_replay_small_case():
+    """The accuracy replay end to end on a small case (64^2 map, 300 lenses,
+    a 2e8-ray brute-force reference, interpolated maps of 1e6 ... 1.6e7
+    rays): lattice sampling error falls with the ray count, so the fitted
+    slope is negative, and the interpolated map of the reference's rays
+    stays close to the brute force."""
+    from gpu_common import require_gpu
+    torch = require_gpu()
+    from paper_2204_10871_gb300 import irs, lensgen
+    out = bench.accuracy_replay(torch, irs, lensgen, ks=0.4, S=8.0, npix=64, n_star=300, ref_rays=2.0e8,
+                                test_rays=(1.0e6, 4.0e6, 1.6e7), reference="brute", ref_chunk_rays=5.0e7,
+                                fit_min=5.0)
+    assert out["reference"]["method"] == "brute" and out["reference"]["bands"] >= 2
+    assert out["reference"]["interp_same_rays_rel_rms"] < 1e-3
+    assert len(out["maps"]) == 3
+    errs = [mp["rel_rms_all_pixels"] for mp in out["maps"]]
+    assert errs[0] > errs[1] > errs[2], errs
+    assert -1.2 < out["slope_all_maps"] < -0.3, out["slope_all_maps"]
