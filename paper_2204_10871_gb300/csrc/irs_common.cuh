@@ -116,6 +116,38 @@ __device__ __forceinline__ void pixel_keys2(float2 t1, float2 t2, uint32_t bx, u
   kb = (pxb < npix_x && pyb < npix_y) ? pyb * npix_x + pxb : 0xFFFFFFFFu;
 }
 
+// pixel_keys2 plus each ray's bin in a box of hbx x hby pixels (lhx, lhy: the
+// box origin folded with the floor's bit pattern offset, as bx, by); ~0u for
+// rays off the map or outside the box.
+__device__ __forceinline__ void pixel_keys2_box(float2 t1, float2 t2, uint32_t bx, uint32_t by,
+                                                uint32_t npix_x, uint32_t npix_y, uint32_t lhx, uint32_t lhy,
+                                                uint32_t hbx, uint32_t hby, uint32_t& ka, uint32_t& kb,
+                                                uint32_t& la, uint32_t& lb) {
+  const float2 f1 = __fadd2_rd(t1, make_float2(PIX_MAGIC, PIX_MAGIC));
+  const float2 f2 = __fadd2_rd(t2, make_float2(PIX_MAGIC, PIX_MAGIC));
+  const uint32_t ua = __float_as_uint(f1.x), va = __float_as_uint(f2.x);
+  const uint32_t ub = __float_as_uint(f1.y), vb = __float_as_uint(f2.y);
+  const uint32_t pxa = ua + bx, pya = va + by, pxb = ub + bx, pyb = vb + by;
+  const bool ina = pxa < npix_x && pya < npix_y, inb = pxb < npix_x && pyb < npix_y;
+  ka = ina ? pya * npix_x + pxa : 0xFFFFFFFFu;
+  kb = inb ? pyb * npix_x + pxb : 0xFFFFFFFFu;
+  const uint32_t xa = ua + lhx, ya = va + lhy, xb = ub + lhx, yb = vb + lhy;
+  la = (ina && xa < hbx && ya < hby) ? ya * hbx + xa : 0xFFFFFFFFu;
+  lb = (inb && xb < hbx && yb < hby) ? yb * hbx + xb : 0xFFFFFFFFu;
+}
+
+// bin_warp_key into a shared-memory sub-histogram where the leader's ray has
+// a box bin (lkey; equal keys have equal bins), into the map otherwise.
+__device__ __forceinline__ void bin_warp_key_box(uint32_t* counts, uint32_t* hist, uint32_t key, uint32_t lkey,
+                                                 unsigned lane_lt) {
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+  if (key != 0xFFFFFFFFu && (peers & lane_lt) == 0u) {
+    const uint32_t n = (uint32_t)__popc(peers);
+    if (lkey != 0xFFFFFFFFu) atomicAdd(hist + lkey, n);
+    else atomicAdd(counts + key, n);
+  }
+}
+
 // ---------------------------------------------------------------- brute force
 constexpr int BR_TX = 32;             // tile columns: one per lane
 constexpr int BR_TY = 64;             // tile rows: 64/R warps of R rows per thread

@@ -90,6 +90,10 @@ struct IpGeo {
   float inv_k;  // 1 / k in FP32 (correctly rounded)
   int32_t nrow;  // row-pair entries of the ray pass's row table: (k + 1)/2 + IP_ROW_PAD
   int32_t pad_;
+  // privatised binning (BIN 2): half extents, in pixels, of the box around a
+  // cell's centre that holds its rays' pixels under the mean lens map, with
+  // room for the near lenses' and the far field's spread
+  float box_hx, box_hy;
 };
 
 struct InterpState {
@@ -631,7 +635,10 @@ struct IpRayArgs {
 // trades one Horner step per ray for a bound of 1.7e-7 (16 sub-cells, 5
 // terms).
 // MINB: CTAs per SM the register budget is sized for; BIN: warp binning by
-// __match_any_sync (0) or by runs of equal pixels (1); NPR: how many of a
+// __match_any_sync (0), by runs of equal pixels (1), or by __match_any_sync
+// into a shared-memory sub-histogram over the cell's pixel box, flushed to
+// the map once per cell, with global atomics for rays outside the box (2);
+// NPR: how many of a
 // thread's R/2 row pairs share one reciprocal per lens, 1/(r_a^2 r_b^2) (the
 // near sum is bound by the MUFU's 16 reciprocals per SM per clock; a shared
 // reciprocal trades one MUFU op for FP32 work on a pipe that is half idle).
@@ -639,8 +646,9 @@ struct IpRayArgs {
   X(0, 8, 12, 6, 3, 0, 0) X(1, 8, 10, 7, 3, 0, 0) X(2, 8, 16, 6, 3, 0, 2)                       \
   X(3, 8, 16, 6, 3, 0, 4) X(4, 8, 16, 6, 2, 1, 0) X(5, 8, 16, 6, 3, 1, 0)                      \
   X(6, 8, 16, 6, 3, 1, 2) X(7, 8, 16, 6, 3, 0, 0) X(8, 4, 16, 6, 4, 0, 0)                      \
-  X(9, 8, 8, 8, 3, 0, 0) X(10, 8, 12, 6, 4, 0, 0) X(11, 8, 16, 5, 3, 0, 0)
-constexpr int IP_NVARIANT = 12;
+  X(9, 8, 8, 8, 3, 0, 0) X(10, 8, 12, 6, 4, 0, 0) X(11, 8, 16, 5, 3, 0, 0)                    \
+  X(12, 8, 16, 5, 3, 2, 0)
+constexpr int IP_NVARIANT = 13;
 
 // Advance a (strip, row group) position by `by` units of a row-major
 // nstrip-wide unit grid.
@@ -671,9 +679,14 @@ constexpr int IP_CB_STRIDE = IP_KMAX + 1;
 // near lenses as (-x, -x, -y, -y) and (-m, -m) pairs, the level-2 series
 // as conj duplicated (c.re, c.re, -c.im, -c.im), the row table and the
 // level-1 series scaled for the re-centring, one row per level-2 term.
+// Bins of the privatised sub-histogram (BIN 2): a cell whose pixel box is
+// larger bins globally.
+constexpr int IP_HIST_MAX = 2048;
+
 // The row table holds `nrow` entries, sized per plan from its cell side
-// (IpGeo::nrow), so that small cells leave shared memory for more CTAs.
-template <int Q, int K2>
+// (IpGeo::nrow), so that small cells leave shared memory for more CTAs; the
+// privatised binning adds its sub-histogram at the end.
+template <int Q, int K2, int BIN>
 struct IpSmem {
   static constexpr size_t near_xy = 0;
   static constexpr size_t near_m = near_xy + sizeof(float4) * IP_NEAR_MAX;
@@ -681,8 +694,11 @@ struct IpSmem {
   static constexpr int nrow_max = IP_KMAX_RAYS / 2 + IP_ROW_PAD;
   static constexpr size_t row_sg = sub + sizeof(float4) * Q * Q * K2;
   static __host__ __device__ constexpr size_t coef(int nrow) { return row_sg + sizeof(IpRowPair) * nrow; }
-  static __host__ __device__ constexpr size_t bytes(int nrow) {
+  static __host__ __device__ constexpr size_t hist(int nrow) {
     return (coef(nrow) + sizeof(float2) * K2 * IP_CB_STRIDE + 15) / 16 * 16;
+  }
+  static __host__ __device__ constexpr size_t bytes(int nrow) {
+    return hist(nrow) + (BIN == 2 ? sizeof(uint32_t) * IP_HIST_MAX : 0);
   }
   static constexpr size_t bytes_max = bytes(nrow_max);
 };
@@ -701,13 +717,14 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
                                         int64_t want_i, int64_t want_j, int64_t work) {
   static_assert(R % 2 == 0, "rows go in pairs");
   static_assert(NPR >= 0 && NPR <= R / 2, "paired row pairs");
-  using L = IpSmem<Q, K2>;
+  using L = IpSmem<Q, K2, BIN>;
   extern __shared__ __align__(16) unsigned char ip_smem[];
   float4* nxy_s = reinterpret_cast<float4*>(ip_smem + L::near_xy);
   float2* nm_s = reinterpret_cast<float2*>(ip_smem + L::near_m);
   float4* sub_s = reinterpret_cast<float4*>(ip_smem + L::sub);
   IpRowPair* row_s = reinterpret_cast<IpRowPair*>(ip_smem + L::row_sg);
   float2* cb_s = reinterpret_cast<float2*>(ip_smem + L::coef(ig.nrow));
+  uint32_t* hist_s = reinterpret_cast<uint32_t*>(ip_smem + L::hist(ig.nrow));
   __shared__ CellRec rec_s;
   __shared__ int blk_start[9], blk_off[10];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -839,6 +856,23 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
     row_s[pr].ty = make_float4(tyv[0], tyv[1], y0[0], y0[1]);
     row_s[pr].v = make_int2(vq[0], vq[1]);
   }
+  // privatised binning: the cell's pixel box [hx0, hx0 + hbx) x [hy0, hy0 + hby)
+  // around the centre's pixel offset (relative to the base pixel; no box when
+  // it exceeds the sub-histogram) and its bins cleared; lhx, lhy turn a ray's
+  // floor bit pattern into its box column and row
+  int32_t hx0 = 0, hy0 = 0, hbx = 0, hby = 0;
+  uint32_t lhx = 0, lhy = 0;
+  if (BIN == 2 && MODE == IP_MAP) {
+    const float cx_pix = __fmul_rn(rec_s.bx_hi, g.inv_sx), cy_pix = __fmul_rn(rec_s.by_hi, g.inv_sy);
+    hx0 = __float2int_rd(__fsub_rn(cx_pix, ig.box_hx));
+    hy0 = __float2int_rd(__fsub_rn(cy_pix, ig.box_hy));
+    hbx = __float2int_rd(__fadd_rn(cx_pix, ig.box_hx)) - hx0 + 1;
+    hby = __float2int_rd(__fadd_rn(cy_pix, ig.box_hy)) - hy0 + 1;
+    if (hbx * hby > IP_HIST_MAX) hbx = hby = 0;
+    lhx = (uint32_t)0u - PIX_MAGIC_BITS - (uint32_t)hx0;
+    lhy = (uint32_t)0u - PIX_MAGIC_BITS - (uint32_t)hy0;
+    for (int t = tid; t < hbx * hby; t += blockDim.x) hist_s[t] = 0u;
+  }
   __syncthreads();
 
   // base pixel of this cell for the 32-bit pixel test, folded with the
@@ -847,6 +881,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
   const uint32_t rbx = (uint32_t)rix - PIX_MAGIC_BITS, rby = (uint32_t)riy - PIX_MAGIC_BITS;
   // the cell centre's beta (hi parts) in pixel units
   const float bxs = __fmul_rn(rec_s.bx_hi, g.inv_sx), bys = __fmul_rn(rec_s.by_hi, g.inv_sy);
+
   const int n_corner = rec_s.n_corner;
   const unsigned lane_lt = (1u << lane) - 1u;
   // cell-local 32-bit lattice indices: columns [0, kx), rows [ylo, yhi); units
@@ -999,7 +1034,7 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
       // beta relative to the base pixel, (by_hi, by_hi) + ((x0, y0) + L_local -
       // alpha_near), in pixel units, then the pixel key of every ray (~0
       // where none)
-      uint32_t key[2 * HP];
+      uint32_t key[2 * HP], lkey[2 * HP];
 #pragma unroll
       for (int i = 0; i < HP; ++i) {
         const float4 t = row_s[p0 + h + i].ty;
@@ -1008,7 +1043,11 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
         const float2 SY = __fadd2_rn(y0, __fadd2_rn(NAY[h + i], QI[i]));
         const float2 T1 = __ffma2_rn(SX, make_float2(g.inv_sx, g.inv_sx), make_float2(bxs, bxs));
         const float2 T2 = __ffma2_rn(SY, make_float2(g.inv_sy, g.inv_sy), make_float2(bys, bys));
-        pixel_keys2(T1, T2, rbx, rby, (uint32_t)g.npix_x, (uint32_t)g.npix_y, key[2 * i], key[2 * i + 1]);
+        if (BIN == 2 && MODE == IP_MAP)
+          pixel_keys2_box(T1, T2, rbx, rby, (uint32_t)g.npix_x, (uint32_t)g.npix_y, lhx, lhy, (uint32_t)hbx,
+                          (uint32_t)hby, key[2 * i], key[2 * i + 1], lkey[2 * i], lkey[2 * i + 1]);
+        else
+          pixel_keys2(T1, T2, rbx, rby, (uint32_t)g.npix_x, (uint32_t)g.npix_y, key[2 * i], key[2 * i + 1]);
         if (MODE == IP_DUMP) {
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
@@ -1025,9 +1064,22 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
       if (MODE == IP_MAP) {
 #pragma unroll
         for (int r = 0; r < 2 * HP; ++r) {
-          if (BIN) bin_warp_runs_key(a.counts, key[r], lane);
+          if (BIN == 2) bin_warp_key_box(a.counts, hist_s, key[r], lkey[r], lane_lt);
+          else if (BIN == 1) bin_warp_runs_key(a.counts, key[r], lane);
           else bin_warp_key(a.counts, key[r], lane_lt);
         }
+      }
+    }
+  }
+  if (BIN == 2 && MODE == IP_MAP && hbx > 0) {
+    // flush the cell's sub-histogram: one global add per non-empty bin (bins
+    // off the map never receive a ray: only on-map keys reach the box)
+    __syncthreads();
+    for (int t = tid; t < hbx * hby; t += blockDim.x) {
+      const uint32_t v = hist_s[t];
+      if (v) {
+        const int by = t / hbx, bx = t - by * hbx;
+        atomicAdd(a.counts + (int64_t)(riy + hy0 + by) * g.npix_x + (rix + hx0 + bx), v);
       }
     }
   }
@@ -1099,7 +1151,7 @@ k_ip_ray_batch(const MapDesc* __restrict__ maps, int nmaps, int64_t nitems,
 // before any launch or graph capture that uses it.
 #define IP_DECL_ATTR(V, R, Q, K2, MINB, BIN, NPR)                                                           \
   case V: {                                                                                            \
-    const int b = (int)IpSmem<Q, K2>::bytes_max;                                                      \
+    const int b = (int)IpSmem<Q, K2, BIN>::bytes_max;                                                      \
     e = cudaFuncSetAttribute(k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR>,                                   \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, b);                         \
     if (e == cudaSuccess)                                                                              \
@@ -1119,7 +1171,7 @@ cudaError_t ip_ray_attributes(int variant) {
 #define IP_DECL_OCC(V, R, Q, K2, MINB, BIN, NPR)                                                       \
   case V:                                                                                         \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR>, \
-                                                  IP_THREADS, IpSmem<Q, K2>::bytes(nrow));        \
+                                                  IP_THREADS, IpSmem<Q, K2, BIN>::bytes(nrow));        \
     break;
 // CTAs per SM of a variant whose row table has `nrow` entries
 int ip_ray_occupancy(int variant, int nrow) {
@@ -1130,7 +1182,7 @@ int ip_ray_occupancy(int variant, int nrow) {
 
 #define IP_DECL_BYTES(V, R, Q, K2, MINB, BIN, NPR) \
   case V:                                          \
-    return IpSmem<Q, K2>::bytes(nrow);
+    return IpSmem<Q, K2, BIN>::bytes(nrow);
 size_t ip_ray_smem(int variant, int nrow) {
   switch (variant) { IP_VARIANTS(IP_DECL_BYTES) default: break; }
   return 0;
@@ -1139,10 +1191,10 @@ size_t ip_ray_smem(int variant, int nrow) {
 #define IP_DECL_LAUNCH(V, R, Q, K2, MINB, BIN, NPR)                                                           \
   case V:                                                                                                \
     if (mode == IP_MAP)                                                                                  \
-      k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes(ig.nrow), \
+      k_ip_ray<IP_MAP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2, BIN>::bytes(ig.nrow), \
                                                    s>>>(g, ig, a);                                           \
     else                                                                                                 \
-      k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes(ig.nrow), \
+      k_ip_ray<IP_DUMP, R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2, BIN>::bytes(ig.nrow), \
                                                     s>>>(g,                                                  \
                                                                                                  ig, a); \
     break;
@@ -1154,7 +1206,7 @@ cudaError_t launch_ip_ray(int variant, int mode, int64_t grid, cudaStream_t s, c
 
 #define IP_DECL_BATCH(V, R, Q, K2, MINB, BIN, NPR)                                                       \
   case V:                                                                                           \
-    k_ip_ray_batch<R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2>::bytes(nrow), s>>>( \
+    k_ip_ray_batch<R, Q, K2, MINB, BIN, NPR><<<(unsigned)grid, IP_THREADS, IpSmem<Q, K2, BIN>::bytes(nrow), s>>>( \
         maps, nmaps, nitems, queue);                                                                \
     break;
 cudaError_t launch_ip_ray_batch(int variant, int64_t grid, cudaStream_t s, const MapDesc* maps,
@@ -1304,6 +1356,11 @@ irs_status interp_plan(irs_plan_t* P) {
   ig.k = k;
   ig.nrow = (int32_t)((k + 1) / 2) + IP_ROW_PAD;
   ig.h = (double)k * g.dx3;
+  // a cell of side h maps to |1 - kappa -+ gamma| h under the mean lens map
+  // (declared kappa_*); half of that in pixels, grown by half for the far
+  // field's and the near lenses' spread, plus two pixels
+  ig.box_hx = (float)(0.75 * fabs(P->lambda1) * ig.h / g.sx + 2.0);
+  ig.box_hy = (float)(0.75 * fabs(P->lambda2) * ig.h / g.sy + 2.0);
   ig.hf = (float)ig.h;
   ig.inv_k = 1.0f / (float)k;
   ig.nrcx = (int32_t)((g.nrx + k - 1) / k);

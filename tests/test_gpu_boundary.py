@@ -118,3 +118,25 @@ def test_crowded_block_reports_overflow():
         dxy, dm = to_dev(torch, xy, m)
         plan.make_map(dxy, dm)
         assert _sync_status(plan) == 0
+
+
+def test_size_limits_are_rejected_at_plan_time():
+    """Limits that the kernels' index arithmetic and FP32 ranges need, checked
+    by irs_plan before any allocation of note: the interpolated ray pass's
+    pixel keys need maps below 2^21 pixels per side (IRS_ERR_OVERFLOW), and
+    the default brute-force kernel's four-row reciprocal needs a plane
+    diagonal of at most 1e4 theta_E (IRS_ERR_UNSUPPORTED; a variant with
+    reciprocals shared by two rows serves such planes)."""
+    require_gpu()
+    _, pl = params_pair(0.3, 0.0, 0.3, (-1.0, 1.0, -1.0, 1.0), (1 << 21, 1), 1e-6, method=irs.IRS_INTERP)
+    with pytest.raises(irs.IrsError) as e:
+        irs.Plan(pl)
+    assert e.value.status == 6
+    big = (-5000.0, 5000.0, -5000.0, 5000.0)
+    _, pb = params_pair(0.1, 0.0, 0.1, big, 16, 1e-3, method=irs.IRS_BRUTE)
+    with pytest.raises(irs.IrsError) as e:
+        irs.Plan(pb)
+    assert e.value.status == 8
+    _, pb11 = params_pair(0.1, 0.0, 0.1, big, 16, 1e-3, method=irs.IRS_BRUTE, kernel_variant=11)
+    with irs.Plan(pb11) as plan:
+        assert plan.info.circle_r * 2 > 1e4
