@@ -243,6 +243,8 @@ def run_ours(args):
     xy, m = lens_field(lensgen, box, w["seed"] + (0 if sharded else 1000 * rank), w)
     dxy = torch.from_numpy(xy).to(dev)
     dm = torch.from_numpy(m).to(dev)
+    torch.cuda.synchronize()
+    t_cold0 = time.perf_counter()  # cold start: tuning (cache miss), plan, first map
     tune = None
     if args.variant >= 0:
         params.kernel_variant = args.variant
@@ -289,7 +291,10 @@ def run_ours(args):
     if sharded:
         s0, s1 = shard.strip_rows(int(info.n_rays_y), world, rank, shard.row_align(plan))
         my_rays = (s1 - s0) * info.n_rays_x
-    for _ in range(args.warmup):
+    step()  # the first map of this workload: the end of its cold start
+    plan.sync()
+    cold_start_s = time.perf_counter() - t_cold0
+    for _ in range(args.warmup - 1):
         step()
     plan.sync()
 
@@ -425,6 +430,9 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "autotune": tune,
+            "cold_start": {"s": cold_start_s,
+                           "includes": "autotuning (no cache), plan creation, first map, wall clock; "
+                                       "lens field already on the device"},
             "learned": learned if learned is not None else extra.get("learned"),
             "high_res": extra.get("high_res"),
             "batched": extra.get("batched"),
@@ -990,23 +998,27 @@ def batched_configs(n_maps=256, seed=4, max_rays=4.0e9):
 def study_batched(args):
     """The batched persistent launch (see batched_measure), as its own JSON line."""
     torch, irs, lensgen = _study_env()
-    print(json.dumps(batched_measure(torch, irs, lensgen, args.batch_maps, args.warmup, args.steps)))
+    print(json.dumps(batched_measure(torch, irs, lensgen, args.batch_maps, args.warmup, args.steps,
+                                     args.batch_cell_mult, args.batch_variant)))
 
 
-def batched_measure(torch, irs, lensgen, n_maps, warmup, steps):
+def batched_measure(torch, irs, lensgen, n_maps, warmup, steps, cell_mult=0.7, variant=11):
     """The batched persistent launch: n_maps uneven maps through
     irs_make_maps_batched (one captured CUDA graph, replayed), against one
     irs_make_map per map on the same plans; per-map and total rays/s, and a
-    bitwise check that both give the same maps.  All plans use the setting
-    the autotuner picks at the paper-mid workload (cells 0.85 x the rule,
-    ray-pass variant 0), since one persistent launch serves one variant."""
+    bitwise check that both give the same maps.  All plans share one
+    setting, since one persistent launch serves one variant: cells 0.7 x the
+    rule with ray-pass variant 11, the fastest of (0.85, 0), (0.85, 11),
+    (0.573, 11) and (0.7, 11) on this batch (2.78, 2.82, 2.73 and 2.88e11
+    rays/s on one GB300)."""
     cfgs = batched_configs(n_maps)
     plans, lens, counts, rays = [], [], [], []
     ws = 0
     for k, c in enumerate(cfgs):
         S = c["S"]
         p = irs.make_params(c["kappa_star"], c["kappa_s"], c["gamma"], (-S / 2, S / 2, -S / 2, S / 2), c["npix"],
-                            c["nav"], n_star=c["n_star"], method=irs.IRS_INTERP, cell_mult=0.85, kernel_variant=0)
+                            c["nav"], n_star=c["n_star"], method=irs.IRS_INTERP, cell_mult=cell_mult,
+                            kernel_variant=variant)
         plan = irs.Plan(p)
         inf = plan.info
         ws += inf.workspace_bytes
@@ -1058,7 +1070,7 @@ def batched_measure(torch, irs, lensgen, n_maps, warmup, steps):
     out = {"study": "batched", "maps": len(cfgs), "total_rays": total,
            "config": "kappa_* 0.1-0.6, kappa_s/kappa {0,0.3,0.6}, gamma 0.1-0.6, 500^2-2000^2 px over "
                      "10-20 theta_E, 1e3-1e5 uniform-mass lenses, 16-100 rays/px (seeded)",
-           "setting": {"cell_mult": 0.85, "kernel_variant": 0},
+           "setting": {"cell_mult": cell_mult, "kernel_variant": variant},
            "batched": {"ms": t_batch, "rays_per_s": total / (t_batch * 1e-3), "steps": steps},
            "sequential": {"ms": t_seq, "rays_per_s": total / (t_seq * 1e-3)},
            "per_map_rays_per_s": {"min": float(per.min()), "median": float(np.median(per)),
@@ -1185,6 +1197,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=30.0,
                     help="--impl reference: host CPU seconds for the oracle's warm-up and timed steps together")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps of the batched study")
+    ap.add_argument("--batch-cell-mult", type=float, default=0.7, help="level-1 cell multiplier of the batched maps")
+    ap.add_argument("--batch-variant", type=int, default=11, help="ray-pass variant of the batched maps")
     ap.add_argument("--rf-list", type=float, nargs="+", default=[4, 8, 16, 32],
                     help="split radii R_f (cells) of the learned study")
     ap.add_argument("--shard", default="replicas", choices=["replicas", "strips"],
