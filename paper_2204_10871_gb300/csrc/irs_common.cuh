@@ -136,6 +136,18 @@ __device__ __forceinline__ void pixel_keys2_box(float2 t1, float2 t2, uint32_t b
   lb = (inb && xb < hbx && yb < hby) ? yb * hbx + xb : 0xFFFFFFFFu;
 }
 
+// Both rays of a row pair (keys ka, kb): lanes whose two keys are equal add
+// 2 to it, the others 1 to ka, in one __match_any_sync on ka (the leader adds
+// its peers plus its peers of weight 2); the kb of lanes whose keys differ
+// go through a second match, run only when such a lane exists.
+__device__ __forceinline__ void bin_warp_pair(uint32_t* counts, uint32_t ka, uint32_t kb, unsigned lane_lt) {
+  const unsigned same = __ballot_sync(0xFFFFFFFFu, ka == kb);
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, ka);
+  if (ka != 0xFFFFFFFFu && (peers & lane_lt) == 0u)
+    atomicAdd(counts + ka, (uint32_t)(__popc(peers) + __popc(peers & same)));
+  if (same != 0xFFFFFFFFu) bin_warp_key(counts, ka == kb ? 0xFFFFFFFFu : kb, lane_lt);
+}
+
 // bin_warp_key into a shared-memory sub-histogram where the leader's ray has
 // a box bin (lkey; equal keys have equal bins), into the map otherwise.
 __device__ __forceinline__ void bin_warp_key_box(uint32_t* counts, uint32_t* hist, uint32_t key, uint32_t lkey,

@@ -637,7 +637,9 @@ struct IpRayArgs {
 // MINB: CTAs per SM the register budget is sized for; BIN: warp binning by
 // __match_any_sync (0), by runs of equal pixels (1), or by __match_any_sync
 // into a shared-memory sub-histogram over the cell's pixel box, flushed to
-// the map once per cell, with global atomics for rays outside the box (2);
+// the map once per cell, with global atomics for rays outside the box (2),
+// or by row pairs (3: a pair whose two rays share a pixel adds 2 in one
+// __match_any_sync; a second one runs only when some lane's pair differs);
 // NPR: how many of a
 // thread's R/2 row pairs share one reciprocal per lens, 1/(r_a^2 r_b^2) (the
 // near sum is bound by the MUFU's 16 reciprocals per SM per clock; a shared
@@ -647,8 +649,8 @@ struct IpRayArgs {
   X(3, 8, 16, 6, 3, 0, 4) X(4, 8, 16, 6, 2, 1, 0) X(5, 8, 16, 6, 3, 1, 0)                      \
   X(6, 8, 16, 6, 3, 1, 2) X(7, 8, 16, 6, 3, 0, 0) X(8, 4, 16, 6, 4, 0, 0)                      \
   X(9, 8, 8, 8, 3, 0, 0) X(10, 8, 12, 6, 4, 0, 0) X(11, 8, 16, 5, 3, 0, 0)                    \
-  X(12, 8, 16, 5, 3, 2, 0)
-constexpr int IP_NVARIANT = 13;
+  X(12, 8, 16, 5, 3, 2, 0) X(13, 8, 16, 5, 3, 3, 0)
+constexpr int IP_NVARIANT = 14;
 
 // Advance a (strip, row group) position by `by` units of a row-major
 // nstrip-wide unit grid.
@@ -1063,10 +1065,16 @@ __device__ __forceinline__ void ip_cell(const Geo& g, const IpGeo& ig, const IpR
       }
       if (MODE == IP_MAP) {
 #pragma unroll
-        for (int r = 0; r < 2 * HP; ++r) {
-          if (BIN == 2) bin_warp_key_box(a.counts, hist_s, key[r], lkey[r], lane_lt);
-          else if (BIN == 1) bin_warp_runs_key(a.counts, key[r], lane);
-          else bin_warp_key(a.counts, key[r], lane_lt);
+        if (BIN == 3) {
+#pragma unroll
+          for (int i = 0; i < HP; ++i) bin_warp_pair(a.counts, key[2 * i], key[2 * i + 1], lane_lt);
+        } else {
+#pragma unroll
+          for (int r = 0; r < 2 * HP; ++r) {
+            if (BIN == 2) bin_warp_key_box(a.counts, hist_s, key[r], lkey[r], lane_lt);
+            else if (BIN == 1) bin_warp_runs_key(a.counts, key[r], lane);
+            else bin_warp_key(a.counts, key[r], lane_lt);
+          }
         }
       }
     }
