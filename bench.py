@@ -184,7 +184,8 @@ def ip_flops_fixed(variant):
 # dram__bytes_write.sum), valid only for the kernel build, workload and cell
 # size they were captured on: (workload, cell multiplier, variant) -> bytes.
 # Source: profiles/k_ip_ray_paper-mid-full.md.
-IP_TRAFFIC = {("paper-mid", 0.57, 11): 106.890752e6 + 3.025408e6}
+IP_TRAFFIC = {("paper-mid", 0.57, 11): 106.890752e6 + 3.025408e6,
+              ("paper-mid", 0.57, 13): 107.035136e6 + 3.787776e6}
 
 
 def mean_near_lenses(info, xy):

@@ -26,8 +26,8 @@ MAPS = [
 
 # Maps of the oracle comparison: uneven kappa, gamma, N_* and sizes, rays per
 # pixel kept low enough that the oracle shoots all of them in ~25 s on 16
-# cores; the last is a 500^2 map with 1e4 lenses (the smallest maps of the
-# 256-map batched workload have this size).
+# cores; a 500^2 map with 1e4 lenses (the smallest maps of the 256-map
+# batched workload have this size) and a map without lenses.
 MAPS_ORACLE = [
     (0.30, 0.00, 0.30, 4.0, 96, 16.0, 400, irs.IRS_INTERP, 0),
     (0.55, 0.25, 0.15, 3.0, 64, 4.0, 900, irs.IRS_INTERP, 1),
@@ -36,6 +36,11 @@ MAPS_ORACLE = [
     (0.20, 0.00, 0.10, 2.0, 40, 16.0, 60, irs.IRS_BRUTE, 0),
     (0.45, 0.05, 0.45, 3.0, 80, 4.0, 2000, irs.IRS_INTERP, 0),
     (0.10, 0.00, 0.10, 10.0, 500, 4.0, 10000, irs.IRS_INTERP, 0),
+    # no lenses: the smooth terms alone; at 10.25 rays per pixel every ray of
+    # the regular lattice lands >= 5.8e-3 pixel from a pixel edge (checked
+    # with the oracle's sizing: a lens-free ray on an edge goes to either side
+    # by rounding, FP64 in the oracle, FP32 here)
+    (0.20, 0.10, 0.20, 3.0, 48, 10.25, 0, irs.IRS_INTERP, 13),
 ]
 
 
