@@ -77,7 +77,7 @@ typedef struct irs_params {
   int32_t kernel_variant; /* INTERP: ray-pass variant 0..13 (rays per thread, level-2 sub-cells,
                              sub-cell terms, CTAs per SM, binning -- into the map or into a
                              per-cell shared-memory sub-histogram --, shared reciprocals);
-                             irs_autotune picks one.  BRUTE: variant 0..13 (rows per thread,
+                             irs_autotune picks one.  BRUTE: variant 0..15 (rows per thread,
                              rows sharing a reciprocal by pairs or by fours, packed FP32x2
                              rows); 0 = default.  Variants with four rows per reciprocal (0, 10,
                              12..15) need a plane diagonal <= 1e4 theta_E
