@@ -74,7 +74,7 @@ typedef struct irs_params {
   double cell_mult;       /* INTERP: level-1 cell side in units of the paper's rule; 0 = default */
   int32_t window;         /* INTERP: cells within this Chebyshev distance sum lenses directly into
                              the series; 0 = default */
-  int32_t kernel_variant; /* INTERP: ray-pass variant 0..13 (rays per thread, level-2 sub-cells,
+  int32_t kernel_variant; /* INTERP: ray-pass variant 0..15 (rays per thread, level-2 sub-cells,
                              sub-cell terms, CTAs per SM, binning -- into the map or into a
                              per-cell shared-memory sub-histogram --, shared reciprocals);
                              irs_autotune picks one.  BRUTE: variant 0..15 (rows per thread,

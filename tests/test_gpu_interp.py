@@ -281,7 +281,7 @@ def test_chunked_rows_add_up():
     assert torch.equal(full, acc)
 
 
-@pytest.mark.parametrize("variant", list(range(14)))
+@pytest.mark.parametrize("variant", list(range(16)))
 @pytest.mark.parametrize("cell_mult", [0.5, 2.0])
 def test_every_tunable_choice_is_exact(variant, cell_mult):
     """The autotuner may pick any ray-pass variant and any cell up to 2 theta_E
