@@ -185,7 +185,8 @@ def ip_flops_fixed(variant):
 # size they were captured on: (workload, cell multiplier, variant) -> bytes.
 # Source: profiles/k_ip_ray_paper-mid-full.md.
 IP_TRAFFIC = {("paper-mid", 0.57, 11): 106.890752e6 + 3.025408e6,
-              ("paper-mid", 0.57, 13): 107.035136e6 + 3.787776e6}
+              ("paper-mid", 0.57, 13): 107.035136e6 + 3.787776e6,
+              ("paper-mid", 0.57, 14): 106.874368e6 + 3.572224e6}
 
 
 def mean_near_lenses(info, xy):
