@@ -73,7 +73,8 @@ typedef struct irs_params {
   int32_t far_order;      /* INTERP: terms of the per-cell far-field series; 0 = default */
   double cell_mult;       /* INTERP: level-1 cell side in units of the paper's rule; 0 = default */
   int32_t window;         /* INTERP: cells within this Chebyshev distance sum lenses directly into
-                             the series; 0 = default */
+                             the series; 0 = default.  MLP: the learned split's radius R_f in
+                             cells; 0 = 8 */
   int32_t kernel_variant; /* INTERP: ray-pass variant 0..15 (rays per thread, level-2 sub-cells,
                              sub-cell terms, CTAs per SM, binning -- into the map or into a
                              per-cell shared-memory sub-histogram --, shared reciprocals);
@@ -231,15 +232,18 @@ irs_status irs_autotune(const irs_params* params, const double* lens_xy, const d
                         irs_tune_result* result, void* stream);
 
 /* ---- Learned far field (no paper counterpart).  An IRS_MLP plan sums, for
- * each level-1 cell, the lenses within a smooth window of R_f = 8 cells
- * directly and takes the rest of the far field -- the "far-far" part minus
- * the sheet's analytic part -- from a coordinate network: Fourier features
+ * each level-1 cell, the lenses within a smooth window of R_f cells
+ * (irs_params.window, default 8: weight 1 out to R_f/2, a C-infinity step to
+ * 0 at R_f) directly and takes the rest of the far field -- the "far-far"
+ * part minus the sheet's analytic part -- from a coordinate network: Fourier features
  * [sin, cos](pi B x) of the cell centre (32 frequencies), three tanh layers of
  * width 64, 8 outputs (4 complex series coefficients).  Cells near the
  * rectangle's corners keep an exact direct sum.  Until irs_mlp_train has run,
  * an IRS_MLP plan computes the exact FFT far field of IRS_INTERP (fallback).
  * The network learns the far field of ONE lens field: make maps with the
- * lenses it was trained on. */
+ * lenses it was trained on.  Its maps are not accurate to the 1e-3 per-pixel
+ * magnification of the series form: the network's deflection error is
+ * ~1e-2 theta_E where ~1e-6 is needed; use IRS_INTERP for production maps. */
 typedef struct irs_mlp_report {
   int64_t samples;       /* training samples (direct sums at random points) */
   int32_t steps;         /* AdamW steps, batch 4096 */
