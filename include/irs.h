@@ -208,8 +208,9 @@ irs_status irs_shoot_rays(irs_plan_t* plan, const double* lens_xy, const double*
  * variants on the given lenses
  * (device arrays as irs_make_map) and write into *tuned a copy of *params with
  * the fastest cell_mult and kernel_variant.  Each candidate's cost per map is
- * its measured cell-list and far-field time plus its ray-pass time on a band
- * of ~2e9 rays scaled to the whole lattice.  `cache_path` (or, when NULL or
+ * its cell size's measured cell-list and far-field time plus its ray-pass time
+ * on a band of ~1e9 rays scaled to the whole lattice (one temporary plan per
+ * cell size; every variant's ray pass is timed on that plan's cells).  `cache_path` (or, when NULL or
  * empty, the environment variable IRS_AUTOTUNE_CACHE) names a JSON-lines file
  * of earlier results keyed by a coarse signature of the parameters; a hit
  * returns at once, a miss appends the new result.  For IRS_BRUTE, *tuned =

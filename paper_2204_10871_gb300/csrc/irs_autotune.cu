@@ -8,10 +8,12 @@
 // cell to warps, so where the rule's cell is at least 128 rays wide the sizes
 // are the multiples of 32 rays from 0.5 to 1.25 rule cells (no idle lanes in
 // a cell's last strip) and the rule itself; narrower rule cells take the
-// multipliers 0.5 ... 2 of the rule.  Each candidate plan makes one warm-up and one
-// timed map restricted to a band of lattice rows holding about 2e9 rays (the
-// whole lattice when smaller); its cost per map is the measured cell-list and
-// far-field time plus the ray-pass time scaled to the full lattice.  Results
+// multipliers 0.5 ... 2 of the rule.  Each cell size makes one plan, one
+// warm-up and one timed map restricted to a band of lattice rows holding
+// about 1e9 rays (the whole lattice when smaller), then times every variant's
+// ray pass alone on that band's cells; a candidate's cost per map is the
+// measured cell-list and far-field time plus its ray-pass time scaled to the
+// full lattice.  Results
 // are kept in a JSON-lines cache file keyed by a coarse signature of the
 // parameters, so a sweep over many similar maps tunes once.
 #include <math.h>
@@ -46,7 +48,7 @@ std::vector<double> cell_candidates(double rule_rays) {
   }
   return m;
 }
-constexpr double BAND_RAYS = 2.0e9;
+constexpr double BAND_RAYS = 1.0e9;
 std::mutex g_file_mu;
 
 // Coarse signature: parameters that change the balance between the near sum,
@@ -104,42 +106,65 @@ void cache_store(const char* path, const std::string& key, double mult, int vari
 // own cell, if larger) near-lens rays would lose the 1e-5 theta_E precision.
 constexpr double MAX_CELL_SIDE = 2.0;
 
-double measure(const irs_params& base, double mult, int variant, const double* xy, const double* mass,
-               int64_t n, uint32_t* counts, double h_rule, cudaStream_t s) {
+// Estimated milliseconds per full map of every ray-pass variant at one cell
+// size (ms[v], negative when a variant cannot run), or false when the size
+// cannot be planned.  One plan per size: a band map gives the far field's
+// and the per-cell series' times (the same for every variant), then each
+// variant's ray pass alone is timed on the band's cells (one warm-up launch,
+// one timed).
+bool measure_size(const irs_params& base, double mult, const double* xy, const double* mass, int64_t n,
+                  uint32_t* counts, double h_rule, cudaStream_t s, std::vector<double>& ms) {
+  ms.assign(irs::interp_num_variants(), -1.0);
   irs_params p = base;
   p.method = IRS_INTERP;
   p.cell_mult = mult;
-  p.kernel_variant = variant;
+  p.kernel_variant = 0;
   irs_plan_t* P = nullptr;
-  if (irs_plan(&p, s, &P) != IRS_OK) return -1.0;
+  if (irs_plan(&p, s, &P) != IRS_OK) return false;
   irs_plan_info info;
   irs_plan_info_get(P, &info);
   if (info.cell_x > fmax(MAX_CELL_SIDE, h_rule) * (1.0 + 1e-9)) {
     irs_plan_destroy(P);
-    return -1.0;
+    return false;
   }
   int64_t rows = (int64_t)ceil(BAND_RAYS / (double)info.n_rays_x);
   if (rows < 2 * info.rays_per_cell_y) rows = 2 * info.rays_per_cell_y;
   if (rows > info.n_rays_y) rows = info.n_rays_y;
   const int64_t r0 = (info.n_rays_y - rows) / 2 / (info.rays_per_cell_y) * info.rays_per_cell_y;
   const int64_t r1 = r0 + rows < info.n_rays_y ? r0 + rows : info.n_rays_y;
-  double est = -1.0;
+  const double scale = (double)info.n_rays_y / (double)(r1 - r0);
+  const int64_t k = info.rays_per_cell_y;
+  const double cell_scale = (double)((info.n_rays_y + k - 1) / k) / (double)((r1 + k - 1) / k - r0 / k);
+  double base_ms = -1.0;  // everything but the ray pass, scaled to the whole lattice
   irs_plan_set_timing(P, 1);
   for (int rep = 0; rep < 2; ++rep) {
     if (irs_make_map_rows(P, xy, mass, n, r0, r1, counts, s) != IRS_OK) break;
     irs_timings t;
     if (irs_plan_timings(P, &t) != IRS_OK || !t.valid) break;
-    if (rep == 1) {  // the band's ray pass and per-cell series scaled to the whole lattice
-      const double scale = (double)info.n_rays_y / (double)(r1 - r0);
-      const int64_t k = info.rays_per_cell_y;
-      const double cell_scale = (double)((info.n_rays_y + k - 1) / k) / (double)((r1 + k - 1) / k - r0 / k);
-      est = (double)(t.ms_total - t.ms_raypass - t.ms_finalize) + (double)t.ms_finalize * cell_scale +
-            (double)t.ms_raypass * scale;
+    if (rep == 1)
+      base_ms = (double)(t.ms_total - t.ms_raypass - t.ms_finalize) + (double)t.ms_finalize * cell_scale;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (base_ms >= 0 && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    for (int v = 0; v < irs::interp_num_variants(); ++v) {
+      if (irs::interp_set_variant(P, v) != IRS_OK) continue;
+      float ray = -1.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        if (irs::interp_raypass_rows(P, r0, r1, counts, s, e0, e1) != IRS_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ray, e0, e1) != cudaSuccess) {
+          ray = -1.f;
+          break;
+        }
+      }
+      if (ray >= 0.f) ms[v] = base_ms + (double)ray * scale;
     }
   }
-  if (irs_plan_sync(P, s) != IRS_OK) est = -1.0;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  if (irs_plan_sync(P, s) != IRS_OK) ms.assign(ms.size(), -1.0);
   irs_plan_destroy(P);
-  return est;
+  return true;
 }
 
 }  // namespace
@@ -193,9 +218,11 @@ extern "C" irs_status irs_autotune(const irs_params* params, const double* lens_
     }
   }
   double best = -1.0;
+  std::vector<double> ms_v;
   for (double m : cell_candidates(rule_rays)) {
-    for (int v = 0; v < irs::interp_num_variants(); ++v) {
-      const double t = measure(*params, m, v, lens_xy, mass, n, counts, h_rule, s);
+    if (!measure_size(*params, m, lens_xy, mass, n, counts, h_rule, s, ms_v)) continue;
+    for (int v = 0; v < (int)ms_v.size(); ++v) {
+      const double t = ms_v[(size_t)v];
       if (t < 0) continue;
       r.candidates++;
       if (m == 1.0 && v == 0) r.ms_default = t;

@@ -1522,6 +1522,35 @@ irs_status interp_run(irs_plan_t* P, const double* xy, const double* mass, int64
   return IRS_OK;
 }
 
+irs_status interp_set_variant(irs_plan_t* P, int variant) {
+  InterpState* S = S_(P);
+  if (!S || variant < 0 || variant >= IP_NVARIANT) return IRS_ERR_ARG;
+  if (ip_ray_attributes(variant) != cudaSuccess) return IRS_ERR_CUDA;
+  S->ig.variant = variant;
+  P->p.kernel_variant = variant;
+  S->grid_ray = P->num_sms * ip_ray_occupancy(variant, S->ig.nrow);
+  return IRS_OK;
+}
+
+irs_status interp_raypass_rows(irs_plan_t* P, int64_t row0, int64_t row1, uint32_t* counts, cudaStream_t s,
+                               cudaEvent_t e0, cudaEvent_t e1) {
+  InterpState* S = S_(P);
+  if (!S || row0 < 0 || row1 <= row0 || row1 > P->g.nry) return IRS_ERR_ARG;
+  const int64_t k = S->ig.k;
+  const int64_t rc0 = (row0 / k) * S->ig.nrcx, rc1 = ((row1 + k - 1) / k) * S->ig.nrcx;
+  IpRayArgs a = ray_args(P);
+  a.counts = counts;
+  a.row0 = row0;
+  a.row1 = row1;
+  a.rc_base = rc0;
+  a.nwork = rc1 - rc0;
+  const int64_t grid = (rc1 - rc0) < S->grid_ray ? (rc1 - rc0) : S->grid_ray;
+  if (cudaEventRecord(e0, s) != cudaSuccess) return IRS_ERR_CUDA;
+  if (launch_ip_ray(S->ig.variant, IP_MAP, grid, s, P->g, S->ig, a) != cudaSuccess) return IRS_ERR_CUDA;
+  if (cudaEventRecord(e1, s) != cudaSuccess) return IRS_ERR_CUDA;
+  return IRS_OK;
+}
+
 irs_status interp_shoot_rays(irs_plan_t* P, const double* xy, const double* mass, int64_t n,
                              const int64_t* idx, int64_t nidx, double* beta, int64_t* pix,
                              cudaStream_t s) {

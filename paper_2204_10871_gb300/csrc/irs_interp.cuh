@@ -17,6 +17,14 @@ irs_status interp_shoot_rays(irs_plan_t* P, const double* xy, const double* mass
                              cudaStream_t s);
 void interp_destroy(irs_plan_t* P);
 
+// --- autotuner (irs_autotune.cu)
+// switch the plan's ray pass to another kernel variant (same cells and far field)
+irs_status interp_set_variant(irs_plan_t* P, int variant);
+// the ray pass alone over lattice rows [row0, row1), on the cell records and
+// series the last map of these rows left, bracketed by events e0, e1 on `s`
+irs_status interp_raypass_rows(irs_plan_t* P, int64_t row0, int64_t row1, uint32_t* counts, cudaStream_t s,
+                               cudaEvent_t e0, cudaEvent_t e1);
+
 // --- batched maps (irs_batch.cu)
 // grow the lens buffers outside any stream capture
 irs_status interp_ensure_capacity(irs_plan_t* P, int64_t n);
