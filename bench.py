@@ -172,7 +172,7 @@ def lens_field(lensgen, box, seed, w=WORKLOAD):
 # same pair arithmetic as the brute force), 8 per complex multiply-add of the
 # level-2 Horner (K2 - 1 of them for K2 series terms), and 20 for the smooth
 # terms, sub-cell index and pixel.
-IP_VARIANT_K2 = [6, 7, 6, 6, 6, 6, 6, 6, 6, 8, 6, 5, 5, 5, 5, 5]  # series terms K2 of ray-pass variants 0..15
+IP_VARIANT_K2 = [6, 7, 6, 6, 6, 6, 6, 6, 6, 8, 6, 5, 5, 5, 5, 5, 4]  # series terms K2 of ray-pass variants 0..16
 IP_FLOPS_OTHER = 20
 
 

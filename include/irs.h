@@ -75,7 +75,7 @@ typedef struct irs_params {
   int32_t window;         /* INTERP: cells within this Chebyshev distance sum lenses directly into
                              the series; 0 = default.  MLP: the learned split's radius R_f in
                              cells; 0 = 8 */
-  int32_t kernel_variant; /* INTERP: ray-pass variant 0..15 (rays per thread, level-2 sub-cells,
+  int32_t kernel_variant; /* INTERP: ray-pass variant 0..16 (rays per thread, level-2 sub-cells,
                              sub-cell terms, CTAs per SM, binning -- into the map or into a
                              per-cell shared-memory sub-histogram --, shared reciprocals);
                              irs_autotune picks one.  BRUTE: variant 0..15 (rows per thread,

@@ -634,7 +634,8 @@ struct IpRayArgs {
 // 0.057, 0.042, so 8, 7, 6 and 6 terms stay at or below ~3e-8; variants 11
 // and 13-15 trade one Horner step per ray for bounds of 1.7e-7 (16 sub-cells,
 // 5 terms), 3.3e-7 (14) and 7.3e-7 (12), the last with fewer sub-cells to
-// re-centre per cell.
+// re-centre per cell; variant 16 takes one more step off with 4 terms on 16
+// sub-cells (3.1e-6, more sub-cells to re-centre).
 // MINB: CTAs per SM the register budget is sized for; BIN: warp binning by
 // __match_any_sync (0), by runs of equal pixels (1), or by __match_any_sync
 // into a shared-memory sub-histogram over the cell's pixel box, flushed to
@@ -650,8 +651,9 @@ struct IpRayArgs {
   X(3, 8, 16, 6, 3, 0, 4) X(4, 8, 16, 6, 2, 1, 0) X(5, 8, 16, 6, 3, 1, 0)                      \
   X(6, 8, 16, 6, 3, 1, 2) X(7, 8, 16, 6, 3, 0, 0) X(8, 4, 16, 6, 4, 0, 0)                      \
   X(9, 8, 8, 8, 3, 0, 0) X(10, 8, 12, 6, 4, 0, 0) X(11, 8, 16, 5, 3, 0, 0)                    \
-  X(12, 8, 16, 5, 3, 2, 0) X(13, 8, 16, 5, 3, 3, 0) X(14, 8, 12, 5, 3, 3, 0) X(15, 8, 14, 5, 3, 3, 0)
-constexpr int IP_NVARIANT = 16;
+  X(12, 8, 16, 5, 3, 2, 0) X(13, 8, 16, 5, 3, 3, 0) X(14, 8, 12, 5, 3, 3, 0) X(15, 8, 14, 5, 3, 3, 0) \
+  X(16, 8, 16, 4, 3, 3, 0)
+constexpr int IP_NVARIANT = 17;
 
 // Advance a (strip, row group) position by `by` units of a row-major
 // nstrip-wide unit grid.

@@ -216,7 +216,7 @@ def test_bad_arguments_raise():
             irs.irs_make_map(plan.handle, buf[1:], m, counts)
         with pytest.raises(ValueError):
             irs.irs_make_map(plan.handle, xy.float(), m, counts)
-    for method, bad in ((irs.IRS_BRUTE, 16), (irs.IRS_BRUTE, -1), (irs.IRS_INTERP, 16)):
+    for method, bad in ((irs.IRS_BRUTE, 16), (irs.IRS_BRUTE, -1), (irs.IRS_INTERP, 17)):
         _, p = params_pair(**C1, method=method, kernel_variant=bad)
         with pytest.raises(irs.IrsError):  # no such kernel variant
             irs.Plan(p)

@@ -191,7 +191,7 @@ def test_c2_at_the_benchmark_configuration():
     xy, m = lenses_for(qo, 100000, shape="salpeter", seed=2, kappa_star=C2[0])
     dxy, dm = to_dev(torch, xy, m)
     tuned, res = irs.irs_autotune(pl, dxy, dm)
-    assert res.candidates > 0 and res.ms_per_map > 0
+    assert (res.from_cache or res.candidates > 0) and res.ms_per_map > 0  # IRS_AUTOTUNE_CACHE may hold it
     err, far, pg, pixo, info = sampled_check(torch, C2, 100000, "salpeter", seed=2, nsamp=1500,
                                              cell_mult=tuned.cell_mult, kernel_variant=tuned.kernel_variant)
     assert err[far].max() <= DEFLECTION_TOL, f"max deflection error {err[far].max():.3e}"
@@ -281,7 +281,7 @@ def test_chunked_rows_add_up():
     assert torch.equal(full, acc)
 
 
-@pytest.mark.parametrize("variant", list(range(16)))
+@pytest.mark.parametrize("variant", list(range(17)))
 @pytest.mark.parametrize("cell_mult", [0.5, 2.0])
 def test_every_tunable_choice_is_exact(variant, cell_mult):
     """The autotuner may pick any ray-pass variant and any cell up to 2 theta_E
