@@ -186,7 +186,8 @@ def ip_flops_fixed(variant):
 # Source: profiles/k_ip_ray_paper-mid-full.md.
 IP_TRAFFIC = {("paper-mid", 0.57, 11): 106.890752e6 + 3.025408e6,
               ("paper-mid", 0.57, 13): 107.035136e6 + 3.787776e6,
-              ("paper-mid", 0.57, 14): 106.874368e6 + 3.572224e6}
+              ("paper-mid", 0.57, 14): 106.874368e6 + 3.572224e6,
+              ("paper-mid", 0.57, 16): 106.763776e6 + 4.427264e6}
 
 
 def mean_near_lenses(info, xy):
@@ -1004,7 +1005,7 @@ def study_batched(args):
                                      args.batch_cell_mult, args.batch_variant)))
 
 
-def batched_measure(torch, irs, lensgen, n_maps, warmup, steps, cell_mult=0.7, variant=11):
+def batched_measure(torch, irs, lensgen, n_maps, warmup, steps, cell_mult=0.7, variant=16):
     """The batched persistent launch: n_maps uneven maps through
     irs_make_maps_batched (one captured CUDA graph, replayed), against one
     irs_make_map per map on the same plans; per-map and total rays/s, and a
@@ -1200,7 +1201,7 @@ def main():
                     help="--impl reference: host CPU seconds for the oracle's warm-up and timed steps together")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps of the batched study")
     ap.add_argument("--batch-cell-mult", type=float, default=0.7, help="level-1 cell multiplier of the batched maps")
-    ap.add_argument("--batch-variant", type=int, default=11, help="ray-pass variant of the batched maps")
+    ap.add_argument("--batch-variant", type=int, default=16, help="ray-pass variant of the batched maps")
     ap.add_argument("--rf-list", type=float, nargs="+", default=[4, 8, 16, 32],
                     help="split radii R_f (cells) of the learned study")
     ap.add_argument("--shard", default="replicas", choices=["replicas", "strips"],
