@@ -126,6 +126,11 @@ struct InterpState {
   float2* conv_f;   // [KF-KD][ncells] local terms KD <= k < KF
   CellRec* recs;   // [nray cells]
   float2* coef;    // [nray cells][K]
+  // the rectangle sheet's corner series per ray cell divided by kappa_*
+  // (geometry only; k_ip_sheet_table), rectangular planes only
+  double2* sheet_d;     // [nray cells][FIN_K64] terms k < FIN_K64
+  float2* sheet_f;      // [nray cells][K - FIN_K64] the rest
+  uint8_t* sheet_near;  // [nray cells] bit q: corner q evaluated per ray instead
   int grid_ray;
 };
 
@@ -396,12 +401,91 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// Corners of the lens rectangle (a1, b1), (a2, b1), (a1, b2), (a2, b2) and
+// the signs of their a_c / kappa_* * pi.
+__device__ __forceinline__ double sheet_corner_x(const Geo& g, int q) { return (q & 1) ? g.a2 : g.a1; }
+__device__ __forceinline__ double sheet_corner_y(const Geo& g, int q) { return (q & 2) ? g.b2 : g.b1; }
+__device__ __forceinline__ double sheet_corner_sign(int q) { return (q == 0 || q == 3) ? 1.0 : -1.0; }
+
+// Per ray cell: the four corner terms of the sheet's analytic part,
+// sum_c -i (a_c / kappa_*) (z - c) Log(z - c), as a series in tau = (z -
+// z_C)/h: terms k < FIN_K64 in FP64, the next K - FIN_K64 in FP32.  They
+// depend on the plan's geometry alone, so a plan builds them once and each
+// map scales them by its kappa_*.  A corner within 4 x 0.71 h of the centre
+// is left out (bit q of `near`): the ray pass evaluates it per ray.
+__global__ void k_ip_sheet_table(Geo g, IpGeo ig, double2* __restrict__ sheet_d, float2* __restrict__ sheet_f,
+                                 uint8_t* __restrict__ sheet_near, int64_t nrc) {
+  const int64_t rc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (rc >= nrc) return;
+  const int cx = (int)(rc % ig.nrcx) + ig.ox, cy = (int)(rc / ig.nrcx) + ig.oy;
+  const double zx = ig.gx0 + (cx + 0.5) * ig.h, zy = ig.gy0 + (cy + 0.5) * ig.h;
+  const double h = ig.h;
+  const int nsf = ig.K - FIN_K64;
+  cd acc[FIN_K64];
+  float2 accf[FIN_K32];
+#pragma unroll
+  for (int k = 0; k < FIN_K64; ++k) acc[k] = {0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < FIN_K32; ++k) accf[k] = make_float2(0.f, 0.f);
+  unsigned near = 0;
+  const double rho = 4.0 * 0.70710678118654752 * h;
+  for (int q = 0; q < 4; ++q) {
+    const double ac = sheet_corner_sign(q) / M_PI;
+    const cd w = {zx - sheet_corner_x(g, q), zy - sheet_corner_y(g, q)};
+    if (hypot(w.re, w.im) < rho) {
+      near |= 1u << q;
+      continue;
+    }
+    // Log(z - c) on the branch that is continuous with the rectangle's
+    // interior: the principal cuts of the two right-hand corners run along
+    // the top and bottom edges, so a cell centre beyond those edges (a
+    // ragged last cell row) takes the argument across the cut.
+    double arg = atan2(w.im, w.re);
+    if (q == 3 && w.re < 0.0 && w.im > 0.0) arg -= 2.0 * M_PI;  // (a2, b2), centre above b2
+    if (q == 1 && w.re < 0.0 && w.im < 0.0) arg += 2.0 * M_PI;  // (a2, b1), centre below b1
+    const cd L = {0.5 * log(w.re * w.re + w.im * w.im), arg};
+    const cd wl = cmul(w, L);
+    acc[0].re += ac * wl.im;
+    acc[0].im -= ac * wl.re;
+    acc[1].re += ac * L.im * h;
+    acc[1].im -= ac * (L.re + 1.0) * h;
+    const cd inv = crecip_nr(w);
+    const cd ih = {inv.re * h, inv.im * h};
+    cd pw = {inv.re * h * h, inv.im * h * h};  // h^n / w^(n-1) at n = 2
+    // n = 2 in FP64 (FIN_K64 = 3), n >= 3 in FP32
+    acc[2].re += ac * 0.5 * pw.im;
+    acc[2].im -= ac * 0.5 * pw.re;
+    pw = cmul(pw, ih);
+    const float2 ihf = make_float2((float)ih.re, (float)ih.im);
+    float2 pf = make_float2((float)pw.re, (float)pw.im);
+    const float acf = (float)ac;
+#pragma unroll
+    for (int k = 0; k < FIN_K32; ++k) {
+      const int n = k + FIN_K64;
+      const float cf = ((n & 1) ? -1.0f : 1.0f) / (float)(n * (n - 1));
+      accf[k].x += acf * cf * pf.y;
+      accf[k].y -= acf * cf * pf.x;
+      pf = cmulf(pf, ihf);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < FIN_K64; ++k) sheet_d[rc * FIN_K64 + k] = make_double2(acc[k].re, acc[k].im);
+#pragma unroll
+  for (int k = 0; k < FIN_K32; ++k) {
+    if (k >= nsf) break;
+    sheet_f[rc * nsf + k] = accf[k];
+  }
+  sheet_near[rc] = (uint8_t)near;
+}
+
 // Per ray cell of [rc0, rc1): window P2L, M2L result, sheet series, centre
 // term, base pixel.
 __global__ void __launch_bounds__(64)
 k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* __restrict__ start,
               const double2* __restrict__ pos, const double* __restrict__ m, const float4* __restrict__ conv_d,
-              const float2* __restrict__ conv_f, MlpFar far, CellRec* __restrict__ recs, float2* __restrict__ coef, int64_t rc0, int64_t rc1) {
+              const float2* __restrict__ conv_f, MlpFar far, const double2* __restrict__ sheet_d,
+              const float2* __restrict__ sheet_f, const uint8_t* __restrict__ sheet_near,
+              CellRec* __restrict__ recs, float2* __restrict__ coef, int64_t rc0, int64_t rc1) {
   const int64_t rc = rc0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (rc >= rc1) return;
   const int cx = (int)(rc % ig.nrcx) + ig.ox, cy = (int)(rc / ig.nrcx) + ig.oy;
@@ -538,55 +622,36 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
   } else if (g.plane == IRS_PLANE_CIRCLE) {
     B = {(1.0 - g.kappa_s - g.gamma) * zx - ks * g.cx, -(1.0 - g.kappa_s + g.gamma) * zy + ks * g.cy};
   } else {
-    // sheet: g(z) = kappa_* (z - 2 a2) + sum_c -i a_c (z - c) Log(z - c); adds g_k h^k
+    // sheet: g(z) = kappa_* (z - 2 a2) + sum_c -i a_c (z - c) Log(z - c); adds
+    // g_k h^k.  a_c = +-kappa_* / pi, so the corner sums are kappa_* times a
+    // per-plan table (k_ip_sheet_table); corners near the cell go to the rays.
     acc[0].re += ks * (zx - 2.0 * g.a2);
     acc[0].im += ks * zy;
     acc[1].re += ks * h;
-    const double rho = 4.0 * 0.70710678118654752 * h;
-    const double cxs[4] = {g.a1, g.a2, g.a1, g.a2};
-    const double cys[4] = {g.b1, g.b1, g.b2, g.b2};
-    const double sgn[4] = {1.0, -1.0, -1.0, 1.0};
-    for (int q = 0; q < 4; ++q) {
-      const double ac = ks / M_PI * sgn[q];
-      if (ac == 0.0) continue;
-      const cd w = {zx - cxs[q], zy - cys[q]};
-      if (hypot(w.re, w.im) < rho && r.n_corner < IP_MAX_CORNER) {
-        r.corner[r.n_corner][0] = (float)w.re;
-        r.corner[r.n_corner][1] = (float)w.im;
-        r.corner[r.n_corner][2] = (float)ac;
+    if (ks != 0.0) {
+      const unsigned near = sheet_near[rc];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (!((near >> q) & 1u)) continue;
+        r.corner[r.n_corner][0] = (float)(zx - sheet_corner_x(g, q));
+        r.corner[r.n_corner][1] = (float)(zy - sheet_corner_y(g, q));
+        r.corner[r.n_corner][2] = (float)(ks / M_PI * sheet_corner_sign(q));
         r.n_corner++;
-        continue;
       }
-      // Log(z - c) on the branch that is continuous with the rectangle's
-      // interior: the principal cuts of the two right-hand corners run along
-      // the top and bottom edges, so a cell centre beyond those edges (a
-      // ragged last cell row) takes the argument across the cut.
-      double arg = atan2(w.im, w.re);
-      if (q == 3 && w.re < 0.0 && w.im > 0.0) arg -= 2.0 * M_PI;  // (a2, b2), centre above b2
-      if (q == 1 && w.re < 0.0 && w.im < 0.0) arg += 2.0 * M_PI;  // (a2, b1), centre below b1
-      const cd L = {0.5 * log(w.re * w.re + w.im * w.im), arg};
-      const cd wl = cmul(w, L);
-      acc[0].re += ac * wl.im;
-      acc[0].im -= ac * wl.re;
-      acc[1].re += ac * L.im * h;
-      acc[1].im -= ac * (L.re + 1.0) * h;
-      const cd inv = crecip_nr(w);
-      const cd ih = {inv.re * h, inv.im * h};
-      cd pw = {inv.re * h * h, inv.im * h * h};  // h^n / w^(n-1) at n = 2
-      // n = 2 in FP64 (FIN_K64 = 3), n >= 3 in FP32
-      acc[2].re += ac * 0.5 * pw.im;
-      acc[2].im -= ac * 0.5 * pw.re;
-      pw = cmul(pw, ih);
-      const float2 ihf = make_float2((float)ih.re, (float)ih.im);
-      float2 pf = make_float2((float)pw.re, (float)pw.im);
-      const float acf = (float)ac;
+#pragma unroll
+      for (int k = 0; k < FIN_K64; ++k) {
+        const double2 t = sheet_d[rc * FIN_K64 + k];
+        acc[k].re += ks * t.x;
+        acc[k].im += ks * t.y;
+      }
+      const int nsf = K - FIN_K64;
+      const float ksf = (float)ks;
 #pragma unroll
       for (int k = 0; k < FIN_K32; ++k) {
-        const int n = k + FIN_K64;
-        const float cf = ((n & 1) ? -1.0f : 1.0f) / (float)(n * (n - 1));
-        accf[k].x += acf * cf * pf.y;
-        accf[k].y -= acf * cf * pf.x;
-        pf = cmulf(pf, ihf);
+        if (k >= nsf) break;
+        const float2 t = sheet_f[rc * nsf + k];
+        accf[k].x = fmaf(ksf, t.x, accf[k].x);
+        accf[k].y = fmaf(ksf, t.y, accf[k].y);
       }
     }
     B = {(1.0 - g.kappa_s - g.gamma) * zx, -(1.0 - g.kappa_s + g.gamma) * zy};
@@ -1324,8 +1389,8 @@ irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* ma
   if (rc1 > rc0)
     k_ip_finalize<<<(unsigned)((rc1 - rc0 + 63) / 64), 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start,
                                                                    S->lens_pos, S->lens_m, S->conv_d,
-                                                                   S->conv_f, far,
-                                                                   S->recs, S->coef, rc0, rc1);
+                                                                   S->conv_f, far, S->sheet_d, S->sheet_f,
+                                                                   S->sheet_near, S->recs, S->coef, rc0, rc1);
   IP_TRY(cudaGetLastError());
   mark(P, EV_FAR, s);
   return IRS_OK;
@@ -1439,6 +1504,10 @@ irs_status interp_plan(irs_plan_t* P) {
   const size_t o_spd = take(sizeof(float4) * IP_PD * G), o_spf = take(sizeof(float2) * (IP_P - IP_PD) * G);
   const size_t o_ksd = take(sizeof(float4) * IP_NKD * G), o_ksf = take(sizeof(float2) * (IP_P + IP_KF - 1) * G);
   const size_t o_rec = take(sizeof(CellRec) * nrc), o_coef = take(sizeof(float2) * ig.K * nrc);
+  const bool rect = p.plane == IRS_PLANE_RECT;
+  const size_t o_shd = take(rect ? sizeof(double2) * FIN_K64 * nrc : 0);
+  const size_t o_shf = take(rect ? sizeof(float2) * (ig.K - FIN_K64) * nrc : 0);
+  const size_t o_shn = take(rect ? sizeof(uint8_t) * nrc : 0);
   if (cudaMalloc(&S->ws, off) != cudaSuccess) {
     cudaGetLastError();
     S->ws = nullptr;
@@ -1460,6 +1529,9 @@ irs_status interp_plan(irs_plan_t* P) {
   S->kspec_f = reinterpret_cast<float2*>(b + o_ksf);
   S->recs = reinterpret_cast<CellRec*>(b + o_rec);
   S->coef = reinterpret_cast<float2*>(b + o_coef);
+  S->sheet_d = rect ? reinterpret_cast<double2*>(b + o_shd) : nullptr;
+  S->sheet_f = rect ? reinterpret_cast<float2*>(b + o_shf) : nullptr;
+  S->sheet_near = rect ? reinterpret_cast<uint8_t*>(b + o_shn) : nullptr;
   irs_status st = alloc_lens_buffers(P, S, nstar + nstar / 4 + 256);
   if (st != IRS_OK) return st;
   // translation kernels and their spectra, once per plan
@@ -1468,6 +1540,10 @@ irs_status interp_plan(irs_plan_t* P) {
   if (cudaGetLastError() != cudaSuccess) return IRS_ERR_CUDA;
   if (fft2d_forward(S->kspec_d, f.Nx, f.Ny, G, S->kspec_d, f, IP_NKD, 0) != cudaSuccess) return IRS_ERR_CUDA;
   if (fft2d_forward(S->kspec_f, f.Nx, f.Ny, G, S->kspec_f, f, nker, 0) != cudaSuccess) return IRS_ERR_CUDA;
+  if (rect && nrc > 0) {  // the sheet's corner series, once per plan
+    k_ip_sheet_table<<<(unsigned)((nrc + 127) / 128), 128>>>(g, ig, S->sheet_d, S->sheet_f, S->sheet_near, nrc);
+    if (cudaGetLastError() != cudaSuccess) return IRS_ERR_CUDA;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) return IRS_ERR_CUDA;
   if (ip_ray_attributes(ig.variant) != cudaSuccess) return IRS_ERR_CUDA;
   S->grid_ray = P->num_sms * ip_ray_occupancy(ig.variant, ig.nrow);
