@@ -114,6 +114,8 @@ struct InterpState {
   float4* lens_rel;
   double2* lens_pos;
   double* lens_m;
+  float4* lens_pdf;  // positions as complex double-float (x.hi, x.lo, y.hi, y.lo)
+  float2* lens_mdf;  // masses as double-float
   // far-field convolution: complex double-float (float4, irs_df.cuh) for
   // the low orders, FP32 (float2) for the rest
   float4* mpole_d;  // [PD][ncells]    multipoles j < PD
@@ -230,7 +232,7 @@ __global__ void k_ip_sortcells(const int32_t* __restrict__ start, int64_t ncells
 __global__ void k_ip_fill(IpGeo ig, const double2* __restrict__ xy, const double* __restrict__ mass,
                           const int32_t* __restrict__ sorted_idx, const int32_t* __restrict__ lens_cell,
                           int64_t n, float4* __restrict__ rel, double2* __restrict__ pos,
-                          double* __restrict__ m_out) {
+                          double* __restrict__ m_out, float4* __restrict__ pos_df, float2* __restrict__ m_df) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int32_t i = sorted_idx[p];
@@ -242,6 +244,8 @@ __global__ void k_ip_fill(IpGeo ig, const double2* __restrict__ xy, const double
   rel[p] = make_float4((float)(q.x - zx), (float)(q.y - zy), (float)m, 0.f);
   pos[p] = q;
   m_out[p] = m;
+  pos_df[p] = dfc_from_double(q.x, q.y);
+  m_df[p] = df_from_double(m);
 }
 
 // ------------------------------------------------------------ far field
@@ -401,6 +405,18 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// 1/(re + i im) in double-float: conj / |.|^2, the reciprocal of |.|^2 from
+// the FP32 reciprocal of its high part and one Newton step r + r (1 - q r)
+// (quadratic convergence: ~2^-47 relative).  |.| >= 1 here (window lenses
+// are at least a cell away, in cell units).
+__device__ __forceinline__ float4 dfc_recip(float2 re, float2 im) {
+  const float2 q = df_add(df_mul(re, re), df_mul(im, im));
+  const float2 r0 = make_float2(__frcp_rn(q.x), 0.f);
+  const float2 e = df_sub(make_float2(1.f, 0.f), df_mul(q, r0));
+  const float2 r = df_add(r0, df_mul(r0, e));
+  return dfc_make(df_mul(re, r), df_neg(df_mul(im, r)));
+}
+
 // Corners of the lens rectangle (a1, b1), (a2, b1), (a1, b2), (a2, b2) and
 // the signs of their a_c / kappa_* * pi.
 __device__ __forceinline__ double sheet_corner_x(const Geo& g, int q) { return (q & 1) ? g.a2 : g.a1; }
@@ -482,7 +498,8 @@ __global__ void k_ip_sheet_table(Geo g, IpGeo ig, double2* __restrict__ sheet_d,
 // term, base pixel.
 __global__ void __launch_bounds__(64)
 k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* __restrict__ start,
-              const double2* __restrict__ pos, const double* __restrict__ m, const float4* __restrict__ conv_d,
+              const double2* __restrict__ pos, const double* __restrict__ m, const float4* __restrict__ pos_df,
+              const float2* __restrict__ m_df, const float4* __restrict__ conv_d,
               const float2* __restrict__ conv_f, MlpFar far, const double2* __restrict__ sheet_d,
               const float2* __restrict__ sheet_f, const uint8_t* __restrict__ sheet_near,
               CellRec* __restrict__ recs, float2* __restrict__ coef, int64_t rc0, int64_t rc1) {
@@ -499,10 +516,15 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
   // FP64, the rest in FP32 (terms past K are computed and dropped)
   cd acc[FIN_K64];
   float2 accf[FIN_K32];
+  float4 accd[FIN_K64];  // the window's terms k < FIN_K64 in double-float (series mode)
 #pragma unroll
-  for (int k = 0; k < FIN_K64; ++k) acc[k] = {0.0, 0.0};
+  for (int k = 0; k < FIN_K64; ++k) {
+    acc[k] = {0.0, 0.0};
+    accd[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 #pragma unroll
   for (int k = 0; k < FIN_K32; ++k) accf[k] = make_float2(0.f, 0.f);
+  const float2 zx_df = df_from_double(zx), zy_df = df_from_double(zy), ih_df = df_from_double(inv_h);
   // direct ring: lenses of cells at Chebyshev distance 2..W (series mode), or
   // every lens outside the near block weighted by w(r) out to R_f (network
   // mode).  The (cell, lens) pairs are walked as one sequence per thread, one
@@ -522,28 +544,46 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
     }
     if (q >= nwin) break;
     const int pl = p++;  // this step's lens (the step always advances)
-    const cd d = {(pos[pl].x - zx) * inv_h, (pos[pl].y - zy) * inv_h};
-    double wm = m[pl];
-    if (far.active) {
-      wm *= mlp_ring_weight(hypot(d.re, d.im), far.rf);
+    float2 invf, pf;
+    if (far.active) {  // network mode: the ring weight wants |d| in FP64
+      const cd d = {(pos[pl].x - zx) * inv_h, (pos[pl].y - zy) * inv_h};
+      const double wm = m[pl] * mlp_ring_weight(hypot(d.re, d.im), far.rf);
       if (wm == 0.0) continue;
-    }
-    const cd inv = crecip_nr(d);
-    cd pw = {wm * inv.re, wm * inv.im};  // + m d^-(k+1)
+      const cd inv = crecip_nr(d);
+      cd pw = {wm * inv.re, wm * inv.im};  // + m d^-(k+1)
 #pragma unroll
-    for (int k = 0; k < FIN_K64; ++k) {
-      acc[k].re += pw.re;
-      acc[k].im += pw.im;
-      pw = cmul(pw, inv);
+      for (int k = 0; k < FIN_K64; ++k) {
+        acc[k].re += pw.re;
+        acc[k].im += pw.im;
+        pw = cmul(pw, inv);
+      }
+      invf = make_float2((float)inv.re, (float)inv.im);
+      pf = make_float2((float)pw.re, (float)pw.im);
+    } else {  // series mode: the same terms in double-float on the FP32 pipes
+      const float4 q4 = pos_df[pl];
+      const float2 dre = df_mul(df_sub(make_float2(q4.x, q4.y), zx_df), ih_df);
+      const float2 dim = df_mul(df_sub(make_float2(q4.z, q4.w), zy_df), ih_df);
+      const float4 inv = dfc_recip(dre, dim);
+      float4 pw = dfc_scale(inv, m_df[pl]);  // + m d^-(k+1)
+#pragma unroll
+      for (int k = 0; k < FIN_K64; ++k) {
+        accd[k] = dfc_add(accd[k], pw);
+        pw = dfc_mul(pw, inv);
+      }
+      invf = make_float2(inv.x, inv.z);
+      pf = make_float2(pw.x, pw.z);
     }
-    const float2 invf = make_float2((float)inv.re, (float)inv.im);
-    float2 pf = make_float2((float)pw.re, (float)pw.im);
 #pragma unroll
     for (int k = 0; k < FIN_K32; ++k) {
       accf[k].x += pf.x;
       accf[k].y += pf.y;
       pf = cmulf(pf, invf);
     }
+  }
+#pragma unroll
+  for (int k = 0; k < FIN_K64; ++k) {
+    acc[k].re += df_to_double(dfc_re(accd[k]));
+    acc[k].im += df_to_double(dfc_im(accd[k]));
   }
   // outer cells through the FFT convolution (series mode)
   if (!far.active) {
@@ -1306,6 +1346,7 @@ irs_status alloc_lens_buffers(irs_plan_t* P, InterpState* S, int64_t cap) {
   const size_t o_cell = take(sizeof(int32_t) * cap), o_sidx = take(sizeof(int32_t) * cap);
   const size_t o_rel = take(sizeof(float4) * cap), o_pos = take(sizeof(double2) * cap);
   const size_t o_m = take(sizeof(double) * cap);
+  const size_t o_pdf = take(sizeof(float4) * cap), o_mdf = take(sizeof(float2) * cap);
   if (cudaMalloc(&S->lens_ws, off) != cudaSuccess) {
     cudaGetLastError();
     S->lens_ws = nullptr;
@@ -1318,6 +1359,8 @@ irs_status alloc_lens_buffers(irs_plan_t* P, InterpState* S, int64_t cap) {
   S->lens_rel = reinterpret_cast<float4*>(b + o_rel);
   S->lens_pos = reinterpret_cast<double2*>(b + o_pos);
   S->lens_m = reinterpret_cast<double*>(b + o_m);
+  S->lens_pdf = reinterpret_cast<float4*>(b + o_pdf);
+  S->lens_mdf = reinterpret_cast<float2*>(b + o_mdf);
   S->lens_ws_bytes = off;
   S->cap = cap;
   return IRS_OK;
@@ -1362,7 +1405,8 @@ irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* ma
     k_ip_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S->lens_cell, n, S->cell_cursor, S->sorted_idx);
     k_ip_sortcells<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(S->cell_start, ncells, S->sorted_idx);
     k_ip_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ig, xy2, mass, S->sorted_idx, S->lens_cell, n,
-                                                         S->lens_rel, S->lens_pos, S->lens_m);
+                                                         S->lens_rel, S->lens_pos, S->lens_m, S->lens_pdf,
+                                                         S->lens_mdf);
   }
   IP_TRY(cudaGetLastError());
   mark(P, EV_CELLS, s);
@@ -1388,7 +1432,8 @@ irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* ma
   mark(P, EV_FIN, s);
   if (rc1 > rc0)
     k_ip_finalize<<<(unsigned)((rc1 - rc0 + 63) / 64), 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start,
-                                                                   S->lens_pos, S->lens_m, S->conv_d,
+                                                                   S->lens_pos, S->lens_m, S->lens_pdf,
+                                                                   S->lens_mdf, S->conv_d,
                                                                    S->conv_f, far, S->sheet_d, S->sheet_f,
                                                                    S->sheet_near, S->recs, S->coef, rc0, rc1);
   IP_TRY(cudaGetLastError());
