@@ -3,12 +3,17 @@
 // (irs_df.cuh: 48-bit significands on the FP32 pipes; float4 elements) or in
 // FP32 (float2 elements).
 //
-// A CTA loads B lines of length L = 3^n3 2^n2 into shared memory in
-// mixed-radix digit-reversed order (B as large as keeps the CTA within 52 KB,
-// so that up to four CTAs share an SM; at least one line, up to 9216
-// double-float or FP32 values), runs n3 radix-3 then n2 radix-2 in-place
-// decimation-in-time stages with a twiddle table W_L^t (t < L/2;
-// W_L^(t + L/2) = -W_L^t) staged beside them, and writes the lines back.
+// A CTA loads B lines of length L = 3^n3 2^n2 into shared memory (B as large
+// as keeps the CTA within 52 KB, so that up to four CTAs share an SM; at
+// least one line, up to 9216 double-float or FP32 values), runs in-place
+// butterfly stages with a twiddle table W_L^t (t < L/2; W_L^(t + L/2) =
+// -W_L^t) staged beside them, and writes the lines back.  Neither direction
+// permutes: the forward transform runs decimation in frequency (n2 radix-2
+// then n3 radix-3 stages) on natural-order input and leaves X[k] at the
+// mixed-radix digit reversal of k; the inverse runs decimation in time (n3
+// radix-3 then n2 radix-2 stages), which takes its input in exactly that
+// order and returns natural order.  The convolution between them is
+// pointwise, so the spectra never need sorting.
 // Rows are contiguous lines; columns are strided lines, loaded B adjacent
 // columns at a time so that each row segment is one coalesced access.  Zero padding is implicit: input elements at or beyond
 // `in_len` read as 0, and only the first `out_len` outputs of a line are
@@ -23,21 +28,6 @@
 namespace irs {
 
 namespace {
-
-// Where input element e goes for the in-place decimation-in-time stages (n3
-// radix-3 stages, then n2 radix-2): the n2 low bits of e reversed, times 3^n3,
-// plus the n3 base-3 digits of e >> n2 reversed.  (For n3 = 0 this is the
-// bit reversal; for n3 > 0 the permutation is not its own inverse.)
-__device__ __forceinline__ unsigned digit_pos(unsigned e, int n3, int n2, unsigned pow3) {
-  const unsigned lo = e & ((1u << n2) - 1u);
-  unsigned hi = e >> n2, r3 = 0;
-  for (int i = 0; i < n3; ++i) {
-    const unsigned q = hi / 3u;
-    r3 = r3 * 3u + (hi - 3u * q);
-    hi = q;
-  }
-  return r3 + pow3 * (n2 > 0 ? (__brev(lo) >> (32 - n2)) : 0u);
-}
 
 // Complex arithmetic of the two element types: float4 is double-float
 // (re.hi, re.lo, im.hi, im.lo), float2 is FP32 (re, im).
@@ -123,15 +113,16 @@ __global__ void __launch_bounds__(512) k_fft_lines(const T* in, T* out, FftLines
   T* x = reinterpret_cast<T*>(sm_raw);  // [B][L]
   T* w = x + (size_t)d.B * d.L;         // [L/2]
   const int L = d.L, B = d.B, n3 = d.n3, n2 = d.n2, half_L = L / 2;
-  unsigned pow3 = 1;
-  for (int i = 0; i < n3; ++i) pow3 *= 3u;
+  int pow3 = 1;
+  for (int i = 0; i < n3; ++i) pow3 *= 3;
   const int64_t line0 = (int64_t)blockIdx.x * B;
   const int64_t goff_in = (int64_t)blockIdx.y * d.in_grid_stride;
   const int64_t goff_out = (int64_t)blockIdx.y * d.out_grid_stride;
   const int nthr = blockDim.x;
   const FastDiv fdL((uint32_t)L), fdB((uint32_t)B), fd3((uint32_t)(L / 3)), fd2((uint32_t)half_L);
   for (int k = threadIdx.x; k < L / 2; k += nthr) w[k] = tw_elem<T>(tw[k]);
-  // load, digit-reversed
+  // load (natural order for the forward transform, the forward transform's
+  // output order for the inverse)
   for (int idx = threadIdx.x; idx < B * L; idx += nthr) {
     int b, e;
     if (d.in_elem_stride == 1) {
@@ -145,42 +136,80 @@ __global__ void __launch_bounds__(512) k_fft_lines(const T* in, T* out, FftLines
     T v = c_zero<T>();
     if (line < d.n_lines && e < d.in_len)
       v = in[goff_in + line * d.in_line_stride + (int64_t)e * d.in_elem_stride];
-    x[b * L + digit_pos((unsigned)e, n3, n2, pow3)] = v;
+    x[b * L + e] = v;
   }
   __syncthreads();
-  int m_prev = 1;  // span of the sub-transforms done so far
-  // radix-3 stages: y_q = sum_r (W_m^(j r) x_r) W_3^(q r);
-  // W_3 = -1/2 -+ i sqrt(3)/2, the halving is exact
-  for (int s = 0; s < n3; ++s) {
-    const int m = m_prev * 3, stride = L / m;
-    const FastDiv fdm((uint32_t)m_prev);
-    for (int t = threadIdx.x; t < B * (L / 3); t += nthr) {
-      const int b = (int)fd3.div((uint32_t)t), k = t - b * (L / 3);
-      const int g = (int)fdm.div((uint32_t)k), j = k - g * m_prev;
-      const int i0 = g * m + j, i1 = i0 + m_prev, i2 = i1 + m_prev;
-      const T a = x[b * L + i0];
-      const T p = c_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
-      const T q = c_mul(x[b * L + i2], tw_at<INV>(w, 2 * j * stride, half_L));
-      radix3(a, p, q, INV, x[b * L + i0], x[b * L + i1], x[b * L + i2]);
+  if (!INV) {
+    // decimation in frequency: the transposes of the inverse's stages in
+    // reverse order -- a radix-2 butterfly adds and subtracts, then twiddles
+    // the difference; a radix-3 butterfly transforms, then twiddles outputs
+    // 1 and 2
+    for (int s = n2 - 1; s >= 0; --s) {
+      const int m_prev = pow3 << s, m = 2 * m_prev, stride = L / m;
+      const FastDiv fdm((uint32_t)m_prev);
+      for (int t = threadIdx.x; t < B * (L / 2); t += nthr) {
+        const int b = (int)fd2.div((uint32_t)t), k = t - b * half_L;
+        const int g = (int)fdm.div((uint32_t)k), j = k - g * m_prev;
+        const int i0 = g * m + j, i1 = i0 + m_prev;
+        const T u = x[b * L + i0], v = x[b * L + i1];
+        x[b * L + i0] = c_add(u, v);
+        x[b * L + i1] = c_mul(c_sub(u, v), tw_at<INV>(w, j * stride, half_L));
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    m_prev = m;
-  }
-  // radix-2 stages
-  for (int s = 0; s < n2; ++s) {
-    const int m = m_prev * 2, stride = L / m;
-    const FastDiv fdm((uint32_t)m_prev);
-    for (int t = threadIdx.x; t < B * (L / 2); t += nthr) {
-      const int b = (int)fd2.div((uint32_t)t), k = t - b * half_L;
-      const int g = (int)fdm.div((uint32_t)k), j = k - g * m_prev;
-      const int i0 = g * m + j, i1 = i0 + m_prev;
-      const T u = x[b * L + i0];
-      const T v = c_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
-      x[b * L + i0] = c_add(u, v);
-      x[b * L + i1] = c_sub(u, v);
+    int m_prev = pow3;
+    for (int s = n3 - 1; s >= 0; --s) {
+      m_prev /= 3;
+      const int m = m_prev * 3, stride = L / m;
+      const FastDiv fdm((uint32_t)m_prev);
+      for (int t = threadIdx.x; t < B * (L / 3); t += nthr) {
+        const int b = (int)fd3.div((uint32_t)t), k = t - b * (L / 3);
+        const int g = (int)fdm.div((uint32_t)k), j = k - g * m_prev;
+        const int i0 = g * m + j, i1 = i0 + m_prev, i2 = i1 + m_prev;
+        T y0, y1, y2;
+        radix3(x[b * L + i0], x[b * L + i1], x[b * L + i2], INV, y0, y1, y2);
+        x[b * L + i0] = y0;
+        x[b * L + i1] = c_mul(y1, tw_at<INV>(w, j * stride, half_L));
+        x[b * L + i2] = c_mul(y2, tw_at<INV>(w, 2 * j * stride, half_L));
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    m_prev = m;
+  } else {
+    // decimation in time
+    int m_prev = 1;  // span of the sub-transforms done so far
+    // radix-3 stages: y_q = sum_r (W_m^(j r) x_r) W_3^(q r);
+    // W_3 = -1/2 -+ i sqrt(3)/2, the halving is exact
+    for (int s = 0; s < n3; ++s) {
+      const int m = m_prev * 3, stride = L / m;
+      const FastDiv fdm((uint32_t)m_prev);
+      for (int t = threadIdx.x; t < B * (L / 3); t += nthr) {
+        const int b = (int)fd3.div((uint32_t)t), k = t - b * (L / 3);
+        const int g = (int)fdm.div((uint32_t)k), j = k - g * m_prev;
+        const int i0 = g * m + j, i1 = i0 + m_prev, i2 = i1 + m_prev;
+        const T a = x[b * L + i0];
+        const T p = c_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
+        const T q = c_mul(x[b * L + i2], tw_at<INV>(w, 2 * j * stride, half_L));
+        radix3(a, p, q, INV, x[b * L + i0], x[b * L + i1], x[b * L + i2]);
+      }
+      __syncthreads();
+      m_prev = m;
+    }
+    // radix-2 stages
+    for (int s = 0; s < n2; ++s) {
+      const int m = m_prev * 2, stride = L / m;
+      const FastDiv fdm((uint32_t)m_prev);
+      for (int t = threadIdx.x; t < B * (L / 2); t += nthr) {
+        const int b = (int)fd2.div((uint32_t)t), k = t - b * half_L;
+        const int g = (int)fdm.div((uint32_t)k), j = k - g * m_prev;
+        const int i0 = g * m + j, i1 = i0 + m_prev;
+        const T u = x[b * L + i0];
+        const T v = c_mul(x[b * L + i1], tw_at<INV>(w, j * stride, half_L));
+        x[b * L + i0] = c_add(u, v);
+        x[b * L + i1] = c_sub(u, v);
+      }
+      __syncthreads();
+      m_prev = m;
+    }
   }
   const bool scaled = d.scale != 1.0;
   for (int idx = threadIdx.x; idx < B * L; idx += nthr) {
