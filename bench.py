@@ -383,7 +383,7 @@ def run_ours(args):
     if clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / (n_sms * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
 
-    # ---- brute force on a band of the same lattice: rays/s and the accuracy judge
+    # ---- brute force on a band of the same lattice: rays/s and the accuracy reference
     brute = None
     if full and not args.no_brute and rank == 0:
         brute = brute_band(irs, torch, w, xy, m, dxy, dm, band, plan, n_sms, peak_tflops, value)
