@@ -347,11 +347,6 @@ cudaError_t fft2d_inverse_t(T* spec, const Fft2d& f, int64_t nx, int64_t ny, T* 
 
 }  // namespace
 
-cudaError_t fft_lines(const float4* in, float4* out, FftLines d, int ngrids, const float4* tw, bool inverse,
-                      cudaStream_t s) {
-  return fft_lines_t(in, out, d, ngrids, tw, inverse, s);
-}
-
 cudaError_t fft2d_forward(const float4* compact, int64_t nx, int64_t ny, int64_t in_grid_stride, float4* spec,
                           const Fft2d& f, int ngrids, cudaStream_t s) {
   return fft2d_forward_t(compact, nx, ny, in_grid_stride, spec, f, ngrids, s);

@@ -35,9 +35,10 @@ struct Fft2d {
 int fft_good_size(int64_t n_min, int* n3, int* n2);
 cudaError_t fft_twiddles(int L, float4** d_tw);
 cudaError_t fft_setup_attributes();
-cudaError_t fft_lines(const float4* in, float4* out, FftLines d, int ngrids, const float4* tw,
-                      bool inverse, cudaStream_t s);
-// compact [ngrids][ny][nx] -> padded spectra [ngrids][Ny][Nx]
+// compact [ngrids][ny][nx] -> padded spectra [ngrids][Ny][Nx], each axis in
+// the forward transform's own order (the mixed-radix digit reversal of the
+// frequency index): only pointwise products and sums of spectra made by these
+// transforms are meaningful before fft2d_inverse, which expects that order
 cudaError_t fft2d_forward(const float4* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
                           float4* spec, const Fft2d& f, int ngrids, cudaStream_t s);
 cudaError_t fft2d_forward(const float2* compact, int64_t nx, int64_t ny, int64_t in_grid_stride,
