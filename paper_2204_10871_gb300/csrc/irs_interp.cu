@@ -495,7 +495,9 @@ __global__ void k_ip_sheet_table(Geo g, IpGeo ig, double2* __restrict__ sheet_d,
 }
 
 // Per ray cell of [rc0, rc1): window P2L, M2L result, sheet series, centre
-// term, base pixel.
+// term, base pixel.  NF: FP32 series terms computed (k = FIN_K64 ...
+// FIN_K64 + NF - 1; at least K - FIN_K64).
+template <int NF>
 __global__ void __launch_bounds__(64)
 k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* __restrict__ start,
               const double2* __restrict__ pos, const double* __restrict__ m, const float4* __restrict__ pos_df,
@@ -515,7 +517,7 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
   // coefficients of tau^k before the 1/h of the lens parts: k < FIN_K64 in
   // FP64, the rest in FP32 (terms past K are computed and dropped)
   cd acc[FIN_K64];
-  float2 accf[FIN_K32];
+  float2 accf[NF];
   float4 accd[FIN_K64];  // the window's terms k < FIN_K64 in double-float (series mode)
 #pragma unroll
   for (int k = 0; k < FIN_K64; ++k) {
@@ -523,7 +525,7 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
     accd[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 #pragma unroll
-  for (int k = 0; k < FIN_K32; ++k) accf[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < NF; ++k) accf[k] = make_float2(0.f, 0.f);
   const float2 zx_df = df_from_double(zx), zy_df = df_from_double(zy), ih_df = df_from_double(inv_h);
   // direct ring: lenses of cells at Chebyshev distance 2..W (series mode), or
   // every lens outside the near block weighted by w(r) out to R_f (network
@@ -574,7 +576,7 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
       pf = make_float2(pw.x, pw.z);
     }
 #pragma unroll
-    for (int k = 0; k < FIN_K32; ++k) {
+    for (int k = 0; k < NF; ++k) {
       accf[k].x += pf.x;
       accf[k].y += pf.y;
       pf = cmulf(pf, invf);
@@ -613,7 +615,7 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
   }
   const float inv_hf = (float)inv_h;
 #pragma unroll
-  for (int k = 0; k < FIN_K32; ++k) {
+  for (int k = 0; k < NF; ++k) {
     accf[k].x *= inv_hf;
     accf[k].y *= inv_hf;
   }
@@ -687,7 +689,7 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
       const int nsf = K - FIN_K64;
       const float ksf = (float)ks;
 #pragma unroll
-      for (int k = 0; k < FIN_K32; ++k) {
+      for (int k = 0; k < NF; ++k) {
         if (k >= nsf) break;
         const float2 t = sheet_f[rc * nsf + k];
         accf[k].x = fmaf(ksf, t.x, accf[k].x);
@@ -708,7 +710,7 @@ k_ip_finalize(Geo g, IpGeo ig, const double* __restrict__ msum, const int32_t* _
   split_df(-B.im - (g.src_y0 + fy * g.sy), r.by_hi, r.by_lo);
   recs[rc] = r;
 #pragma unroll
-  for (int k = 0; k < IP_KMAX; ++k) {
+  for (int k = 0; k < FIN_K64 + NF; ++k) {
     if (k >= K) break;
     coef[rc * K + k] = k < FIN_K64 ? make_float2((float)acc[k].re, (float)acc[k].im) : accf[k - FIN_K64];
   }
@@ -1430,12 +1432,19 @@ irs_status build_cells_and_far(irs_plan_t* P, const double* xy, const double* ma
   const int64_t nrc = (int64_t)ig.nrcx * ig.nrcy;
   if (rc1 < 0 || rc1 > nrc) rc1 = nrc;
   mark(P, EV_FIN, s);
-  if (rc1 > rc0)
-    k_ip_finalize<<<(unsigned)((rc1 - rc0 + 63) / 64), 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start,
-                                                                   S->lens_pos, S->lens_m, S->lens_pdf,
-                                                                   S->lens_mdf, S->conv_d,
-                                                                   S->conv_f, far, S->sheet_d, S->sheet_f,
-                                                                   S->sheet_near, S->recs, S->coef, rc0, rc1);
+  if (rc1 > rc0) {
+    // the default K = 24 needs 21 FP32 terms; larger K the full FIN_K32
+    const unsigned nb = (unsigned)((rc1 - rc0 + 63) / 64);
+    if (ig.K - FIN_K64 <= 21)
+      k_ip_finalize<21><<<nb, 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start, S->lens_pos, S->lens_m,
+                                          S->lens_pdf, S->lens_mdf, S->conv_d, S->conv_f, far, S->sheet_d,
+                                          S->sheet_f, S->sheet_near, S->recs, S->coef, rc0, rc1);
+    else
+      k_ip_finalize<FIN_K32><<<nb, 64, 0, s>>>(P->g, ig, P->d_msum, S->cell_start, S->lens_pos, S->lens_m,
+                                               S->lens_pdf, S->lens_mdf, S->conv_d, S->conv_f, far,
+                                               S->sheet_d, S->sheet_f, S->sheet_near, S->recs, S->coef, rc0,
+                                               rc1);
+  }
   IP_TRY(cudaGetLastError());
   mark(P, EV_FAR, s);
   return IRS_OK;
