@@ -263,6 +263,54 @@ def test_interp_edge_cases():
     assert torch.equal(a, b)
 
 
+def test_single_lens_through_each_far_field_route():
+    """One lens and rays at every distance from it: in its 3x3 block of
+    level-1 cells (the per-ray near sum), at Chebyshev distance 2-3 (the
+    direct window, terms 0-2 in double-float) and beyond (the FFT multipole
+    convolution).  Each route must give the oracle's beta to 1e-6 theta_E,
+    ten times tighter than the deflection bar, so that a precision loss in
+    any one route shows (rays within 0.3 theta_E of the lens excepted: there
+    the FP32 cell-relative lens position alone moves the near term by
+    ~5e-7)."""
+    torch = require_gpu()
+    cfg = (0.3, 0.1, 0.2, (-1.0, 1.0, -1.0, 1.0), 40, 16.3)
+    po, pl = params_pair(*cfg, method=irs.IRS_INTERP, n_star=400)
+    qo = oracle.size(po)
+    with irs.Plan(pl) as plan:
+        info = plan.info
+        h = info.cell_x
+        lx = info.lens_x0 + 0.37 * (info.lens_x1 - info.lens_x0)
+        ly = info.lens_y0 + 0.61 * (info.lens_y1 - info.lens_y0)
+        xy = np.array([[lx, ly]])
+        m = np.array([0.7])
+        rng = np.random.default_rng(31)
+        idx = np.concatenate([rng.integers(0, qo.n_rays, 6000),
+                              # rays on a grid around the lens, so that the near and window
+                              # routes are well populated
+                              ((np.clip(((ly - qo.b1) / qo.dx3 + rng.uniform(-4.5, 4.5, 3000) * h / qo.dx3)
+                                        .astype(np.int64), 0, qo.nry - 1)) * qo.nrx
+                               + np.clip(((lx - qo.a1) / qo.dx3 + rng.uniform(-4.5, 4.5, 3000) * h / qo.dx3)
+                                         .astype(np.int64), 0, qo.nrx - 1))])
+        _, bo, _ = oracle.shoot_rays(po, qo, xy, m, idx)
+        dxy, dm = to_dev(torch, xy, m)
+        beta, _ = plan.shoot_rays(dxy, dm, torch.from_numpy(idx).cuda())
+        plan.sync()
+    err = np.abs(beta.cpu().numpy() - bo).max(1)
+    t = ray_positions(qo, idx)
+    # Chebyshev distance in level-1 cells between the ray's cell and the lens's
+    cell = lambda v, lo: np.floor((v - lo) / h).astype(np.int64)
+    cheb = np.maximum(np.abs(cell(t[:, 0], info.lens_x0) - cell(lx, info.lens_x0)),
+                      np.abs(cell(t[:, 1], info.lens_y0) - cell(ly, info.lens_y0)))
+    dist = np.hypot(t[:, 0] - lx, t[:, 1] - ly)
+    routes = {"near": (cheb <= 1) & (dist > 0.3), "window": (cheb >= 2) & (cheb <= info.window),
+              "fft": cheb > info.window}
+    print("\n" + ", ".join(f"{name}: {sel.sum()} rays, max error {err[sel].max():.2e}"
+                             for name, sel in routes.items()))
+    for name, sel in routes.items():
+        assert sel.sum() >= 200, f"{name}: only {sel.sum()} rays"
+        assert err[sel].max() <= 1e-6, f"{name}: max beta error {err[sel].max():.3e}"
+
+
 def test_chunked_rows_add_up():
     """irs_make_map_rows over disjoint bands sums to the full map."""
     torch = require_gpu()
